@@ -1,0 +1,420 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: numpy's FFT
+or a brute-force sum, analytic eigenfunctions, the paper's closed-form 4x4
+inverse (eq. "inverse S"), dense matrices assembled from the operator and
+inverted by an independent LU, the exact ODE for spatially uniform fields,
+invariants of the midpoint scheme (Sec. 3.3 Prop. "nodal constraint and
+discrete energy law"), the paper's printed constants (tests/golden) and
+central finite differences for the adjoint.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2607_15290_b300 import inputs as I
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+@pytest.fixture(params=[O.DFT, O.FFT], ids=["dft", "fft"])
+def transform_mode(request):
+    O.set_transform(request.param)
+    yield request.param
+    O.set_transform(O.DFT)
+
+
+# ------------------------------------------------------------------ transforms (Sec. 2.3)
+
+@pytest.mark.parametrize("n", [(8, 4), (4, 8, 2), (16, 16)])
+def test_transform_matches_numpy(n, transform_mode):
+    g = O.Grid(n)
+    rng = np.random.default_rng(1)
+    z = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    got = O.transform(g, z, -1)
+    assert np.allclose(got, np.fft.fftn(z), atol=1e-11 * np.abs(z).sum())
+    back = O.transform(g, got, +1) / g.nodes
+    assert np.allclose(back, z, atol=1e-13)
+
+
+def test_transform_brute_force_nonseparable():
+    """Full non-separable DFT sum on a 4x4 grid."""
+    g = O.Grid((4, 4))
+    rng = np.random.default_rng(2)
+    z = rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape)
+    ref = np.zeros_like(z)
+    for ky in range(4):
+        for kx in range(4):
+            s = 0
+            for y in range(4):
+                for x in range(4):
+                    s += z[y, x] * np.exp(-2j * np.pi * (kx * x + ky * y) / 4)
+            ref[ky, kx] = s
+    assert np.allclose(O.transform(g, z, -1), ref, atol=1e-12)
+
+
+# ------------------------------------------------------------------ Laplacian symbol (Sec. 2.3)
+
+@pytest.mark.parametrize("n,L", [((16, 8), (1.0, 2.0)), ((8, 4, 8), (2 * np.pi,) * 3)])
+def test_spectral_laplacian_eigenfunction(n, L):
+    g = O.Grid(n, L)
+    X = I.coords(n, L)
+    kv = [1, 2, 3][: len(n)]
+    phase = sum(2 * np.pi * k * x / Li for k, x, Li in zip(kv, X, L)) + 0.3
+    u = np.cos(phase)
+    xi2 = sum((2 * np.pi * k / Li) ** 2 for k, Li in zip(kv, L))
+    assert np.allclose(O.neg_laplacian(g, u), xi2 * u, atol=1e-10 * xi2)
+    assert math.isclose(O.symbol(g, kv), xi2, rel_tol=1e-14)
+
+
+def test_spectral_nyquist_counts_full():
+    """max |xi|^2 = N^2/2 on (0, 2pi)^2 (Sec. 4.5): the Nyquist mode has |k| = N/2."""
+    g = O.Grid((16, 16), (2 * np.pi, 2 * np.pi))
+    assert math.isclose(O.symbol(g, (-8, -8)), 16 ** 2 / 2, rel_tol=1e-14)
+    X = I.coords((16, 16), g.L)
+    u = np.cos(8 * X[0])     # the Nyquist mode along x
+    assert np.allclose(O.neg_laplacian(g, u), 64.0 * u, atol=1e-10)
+
+
+def test_fd2_symbol_is_the_five_point_stencil():
+    n, L = (16, 8), (1.0, 0.5)
+    g = O.Grid(n, L)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(g.shape)
+    hx, hy = L[0] / n[0], L[1] / n[1]
+    ref = -(np.roll(u, 1, 1) - 2 * u + np.roll(u, -1, 1)) / hx ** 2 \
+          - (np.roll(u, 1, 0) - 2 * u + np.roll(u, -1, 0)) / hy ** 2
+    assert np.allclose(O.neg_laplacian(g, u, O.FD2), ref, atol=1e-9 * np.abs(ref).max())
+
+
+# ------------------------------------------------------------------ Algorithm 1 and the nodal inverse
+
+def test_hermitian_solve_single_mode():
+    n, L = (16, 16), (1.0, 1.0)
+    g = O.Grid(n, L)
+    prm = O.Params(alpha=0.1, k=3e-3, theta=1.0, lam=0.5)
+    X = I.coords(n, L)
+    u = np.cos(2 * np.pi * (3 * X[0] - 2 * X[1]))
+    sig = (2 * np.pi * 3) ** 2 + (2 * np.pi * 2) ** 2
+    p = np.stack([u, 2 * u, -u, np.full(g.shape, 0.7)])
+    w = O.hermitian_solve(g, prm, p)
+    d = prm.alpha + prm.lam + prm.theta * prm.k * (1 + prm.alpha ** 2) * sig
+    assert np.allclose(w[:3], p[:3] / d, atol=1e-14)
+    assert np.allclose(w[3], 0.7 / prm.lam, atol=1e-15)
+
+
+def closed_form_inverse(m, lam):
+    """The paper's explicit inverse of (S~_i + lambda I), eq. (inverse S), with p = m / lambda."""
+    p1, p2, p3 = m / lam
+    M = np.array([[1, p3, -p2, -p1],
+                  [-p3, 1, p1, -p2],
+                  [p2, -p1, 1, -p3],
+                  [p1, p2, p3, 1]])
+    return M / (lam * (p1 * p1 + p2 * p2 + p3 * p3 + 1))
+
+
+def test_nodal_solve_matches_closed_form():
+    n = (4, 4)
+    g = O.Grid(n)
+    rng = np.random.default_rng(4)
+    m = rng.standard_normal((3,) + g.shape) * 1.3   # non-unit nodes too
+    w = rng.standard_normal((4,) + g.shape)
+    for lam in (0.25, 0.5, 2.0):
+        prm = O.Params(lam=lam)
+        z = O.nodal_solve(g, prm, m, w)
+        zt = O.nodal_solve(g, prm, m, w, transpose=True)
+        for j in np.ndindex(g.shape):
+            Minv = closed_form_inverse(m[(slice(None),) + j], lam)
+            assert np.allclose(z[(slice(None),) + j], Minv @ w[(slice(None),) + j], atol=1e-14)
+            assert np.allclose(zt[(slice(None),) + j], Minv.T @ w[(slice(None),) + j], atol=1e-14)
+
+
+def test_nodal_block_scaled_orthogonal():
+    """(lambda I + S~_i)^T (lambda I + S~_i) = (lambda^2 + |m_i|^2) I (eq. local-scaled-orthogonal):
+    the solve therefore shrinks norms by exactly (lambda^2 + |m|^2)^{-1/2}."""
+    g = O.Grid((4, 2))
+    rng = np.random.default_rng(5)
+    m = rng.standard_normal((3,) + g.shape)
+    w = rng.standard_normal((4,) + g.shape)
+    lam = 0.5
+    z = O.nodal_solve(g, O.Params(lam=lam), m, w)
+    s = lam ** 2 + np.sum(m * m, axis=0)
+    assert np.allclose(np.sum(z * z, axis=0) * s, np.sum(w * w, axis=0), rtol=1e-13)
+
+
+# ------------------------------------------------------------------ saddle matrix structure (Sec. 2.4, 3.1)
+
+def _dense(grid, prm, m):
+    A = O.saddle_dense(grid, prm, m)
+    N = grid.nodes
+    return A, N
+
+
+@pytest.mark.parametrize("exchange", [O.SPECTRAL, O.FD2])
+def test_saddle_blocks(exchange):
+    g = O.Grid((4, 4), (1.0, 1.0))
+    m = I.random_unit(g.n, seed=6) * 1.0
+    prm = O.Params(alpha=0.2, k=1e-2, theta=1.0, exchange=exchange)
+    A, N = _dense(g, prm, m)
+    H = 0.5 * (A + A.T)
+    S = 0.5 * (A - A.T)
+    # Hermitian part = diag(H_v, 0) with sigma(H_v) in [alpha, beta_N] (Cor. Fourier enclosure)
+    assert np.allclose(H[3 * N:, :], 0, atol=1e-14) and np.allclose(H[:, 3 * N:], 0, atol=1e-14)
+    ev = np.linalg.eigvalsh(H[:3 * N, :3 * N])
+    assert ev.min() >= prm.alpha - 1e-12
+    assert ev.max() <= O.beta_N(g, prm) + 1e-9
+    assert math.isclose(ev.min(), prm.alpha, rel_tol=1e-10)
+    assert math.isclose(ev.max(), O.beta_N(g, prm), rel_tol=1e-10)
+    # constraint block: -B with B B^T = diag |m_i|^2 (Prop. well-posedness)
+    Bneg = A[3 * N:, :3 * N]
+    assert np.allclose(-Bneg @ -Bneg.T, np.diag(np.sum(m * m, axis=0).ravel()), atol=1e-14)
+    # skew part is nodal: m x v and m r (eqs. (S), (Lambda))
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(4 * N)
+    v = x[:3 * N].reshape(3, N)
+    r = x[3 * N:]
+    mm = m.reshape(3, N)
+    ref = np.concatenate([(np.cross(mm.T, v.T).T + mm * r).ravel(), -np.sum(mm * v, axis=0)])
+    assert np.allclose(S @ x, ref, atol=1e-13)
+
+
+def test_saddle_nonsingular_and_transpose():
+    g = O.Grid((4, 4, 4))
+    m = I.random_unit(g.n, seed=8)
+    prm = O.Params(alpha=0.1, k=2e-2, theta=0.5)
+    A, N = _dense(g, prm, m)
+    assert np.linalg.matrix_rank(A) == 4 * N
+    x = np.random.default_rng(9).standard_normal(4 * N)
+    assert np.allclose(O.saddle_apply(g, prm, m, x, transpose=True).ravel(), A.T @ x, atol=1e-12)
+
+
+# ------------------------------------------------------------------ preconditioner identities (Sec. 3.2, 3.4)
+
+@pytest.mark.parametrize("dims", [(4, 4), (8, 4), (4, 2, 4)])
+def test_preconditioner_inverts_the_split_product(dims):
+    """M_lambda = (H + lambda I)(S + lambda I) built from the dense Hermitian/skew parts of A;
+    the oracle's apply must be its inverse (and the transposed apply the inverse of M^T)."""
+    g = O.Grid(dims)
+    m = I.random_unit(dims, seed=10)
+    prm = O.Params(alpha=0.2, k=1e-2, theta=1.0, lam=0.5)
+    A, N = _dense(g, prm, m)
+    n = 4 * N
+    Hf, Sf = 0.5 * (A + A.T), 0.5 * (A - A.T)
+    M = (Hf + prm.lam * np.eye(n)) @ (Sf + prm.lam * np.eye(n))
+    p = np.random.default_rng(11).standard_normal(n)
+    z = O.ffthss_apply(g, prm, m, p).ravel()
+    assert np.allclose(M @ z, p, atol=1e-12)
+    zt = O.ffthss_apply(g, prm, m, p, transpose=True).ravel()
+    assert np.allclose(M.T @ zt, p, atol=1e-12)
+
+
+def test_preconditioned_operator_is_half_identity_minus_T():
+    """P_lambda = M^{-1} A = (2 lambda)^{-1} (I - T_lambda) (proof of Thm. full-saddle GMRES)."""
+    g = O.Grid((4, 4))
+    m = I.random_unit(g.n, seed=12)
+    prm = O.Params(alpha=0.2, k=1e-2, theta=1.0, lam=0.5)
+    A, N = _dense(g, prm, m)
+    n, lam = 4 * N, prm.lam
+    Hf, Sf = 0.5 * (A + A.T), 0.5 * (A - A.T)
+    Id = np.eye(n)
+    T = np.linalg.solve(lam * Id + Sf, (lam * Id - Hf) @ np.linalg.solve(lam * Id + Hf, lam * Id - Sf))
+    x = np.random.default_rng(13).standard_normal(n)
+    lhs = O.ffthss_apply(g, prm, m, O.saddle_apply(g, prm, m, x)).ravel()
+    assert np.allclose(lhs, (x - T @ x) / (2 * lam), atol=1e-12)
+
+
+# ------------------------------------------------------------------ GMRES (Sec. 3.2, Sec. 4.1)
+
+@pytest.mark.parametrize("dims,theta", [((4, 4), 1.0), ((8, 8), 0.5), ((4, 4, 4), 1.0)])
+def test_gmres_matches_dense_lu(dims, theta):
+    g = O.Grid(dims)
+    m = I.random_unit(dims, seed=14)
+    prm = O.Params(alpha=0.1, k=5e-3, theta=theta, lam=0.5, h=(0.0, 0.0, 0.5))
+    A, N = _dense(g, prm, m)
+    b = I.random_saddle_vector(dims, seed=15, zero_r=True)
+    x_lu = np.linalg.solve(A, b.ravel())          # numpy LU, independent of the oracle
+    x, info = O.gmres_solve(g, prm, O.Opts(restart=30, rtol=1e-12), m, b)
+    assert info.converged and info.rel_res_true <= 1e-12
+    assert np.linalg.norm(x.ravel() - x_lu) <= 1e-9 * np.linalg.norm(x_lu)
+    # tangent constraint m.v = 0 at every node
+    assert np.abs(np.sum(m * x[:3], axis=0)).max() <= 1e-10 * np.abs(x).max()
+    x_d, _ = O.gmres_solve(g, prm, O.Opts(use_dense=1), m, b)
+    assert np.allclose(x_d.ravel(), x_lu, atol=1e-11 * np.abs(x_lu).max())
+
+
+def test_gmres_even_step_bound():
+    """||r_2j|| / ||r_0|| <= kappa_lambda theta_2^j for unrestarted GMRES (eq. full-gmres-bound)."""
+    g = O.Grid((8, 8), (2 * np.pi, 2 * np.pi))
+    m = I.random_unit(g.n, seed=16) * 1.0
+    nrm = np.sqrt(np.sum(m * m, axis=0))
+    prm = O.Params(alpha=0.2, k=10.24 / 64, theta=1.0, lam=0.5)
+    b = I.random_saddle_vector(g.n, seed=17)
+    x, info = O.gmres_solve(g, prm, O.Opts(restart=400, rtol=1e-13), m, b, hist_len=400)
+    hist = info.extra["hist"]
+    beta = O.beta_N(g, prm)
+    q = O.q_bar(prm.lam, prm.alpha, beta)
+    gam = O.gamma_m(prm.lam, nrm.min(), nrm.max())
+    th = O.theta2(q, gam)
+    kap = O.kappa(prm.lam, nrm.min(), nrm.max())
+    for j in range(1, len(hist) // 2 + 1):
+        assert hist[2 * j - 1] <= kap * th ** j * (1 + 1e-9)
+    assert info.iters <= O.iteration_bound(kap, th, 1e-13)
+
+
+# ------------------------------------------------------------------ closed forms vs the paper's printed values
+
+def test_bounded_stiffness_constants():
+    G = GOLD["bounded_stiffness"]
+    for N in G["grids"]:
+        g = O.Grid((N, N), (2 * np.pi, 2 * np.pi))
+        prm = O.Params(alpha=G["alpha"], lam=G["lambda"], theta=G["theta"], k=G["kN2"] / N ** 2)
+        beta = O.beta_N(g, prm)
+        assert abs(beta - prm.alpha - G["k_chat_sigma_max"]["value"]) <= G["k_chat_sigma_max"]["tol"]
+        assert abs(beta - G["beta_N"]["value"]) <= G["beta_N"]["tol"]
+        q = O.q_bar(prm.lam, prm.alpha, beta)
+        assert abs(q - G["q_H"]["value"]) <= G["q_H"]["tol"]
+        th = O.theta2(q, O.gamma_m(prm.lam, 1.0, 1.0))
+        assert abs(th - G["theta2"]["value"]) <= G["theta2"]["tol"]
+        ratio = (beta - prm.alpha) / (2 * prm.alpha)     # eq. explicit-exchange-cfl
+        assert abs(ratio - G["explicit_limit_ratio"]["value"]) <= G["explicit_limit_ratio"]["tol"]
+        assert abs(beta / prm.alpha - G["condition_number_H"]["value"]) <= G["condition_number_H"]["tol"]
+
+
+def test_fixed_k_theta2_and_lambda_bd():
+    G = GOLD["fixed_k_theta2"]
+    for N, ref in zip(G["N"], G["value"]):
+        g = O.Grid((N, N), (2 * np.pi, 2 * np.pi))
+        prm = O.Params(alpha=G["alpha"], lam=G["lambda"], theta=G["theta"], k=G["k"])
+        q = O.q_bar(prm.lam, prm.alpha, O.beta_N(g, prm))
+        assert abs(O.theta2(q, O.gamma_m(prm.lam, 1.0, 1.0)) - ref) <= G["tol"]
+    G = GOLD["lambda_bd"]
+    for N, ref in zip(G["N"], G["value"]):
+        g = O.Grid((N, N), (2 * np.pi, 2 * np.pi))
+        prm = O.Params(alpha=G["alpha"], theta=G["theta"], k=G["k"])
+        assert abs(O.lambda_bd(prm.alpha, O.beta_N(g, prm)) - ref) <= G["tol"]
+
+
+# ------------------------------------------------------------------ time steppers vs the exact uniform-field ODE
+
+def _uniform(theta0, phi0, shape):
+    m = np.array([np.sin(theta0) * np.cos(phi0), np.sin(theta0) * np.sin(phi0), np.cos(theta0)])
+    return np.broadcast_to(m.reshape(3, *([1] * len(shape))), (3,) + shape).copy()
+
+
+def _exact_uniform(theta0, phi0, H, alpha, t):
+    """Exact solution of dm/dt = -m x h - alpha m x (m x h) for h = H e3:
+    tan(theta/2) = tan(theta0/2) exp(-alpha H t), phi = phi0 + H t."""
+    th = 2 * np.arctan(np.tan(theta0 / 2) * np.exp(-alpha * H * t))
+    ph = phi0 + H * t
+    return np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+
+
+def test_euler_velocity_is_llg_rhs_for_uniform_field():
+    g = O.Grid((4, 4))
+    H, alpha = 0.5, 0.1
+    m = _uniform(1.0, 0.3, g.shape)
+    prm = O.Params(alpha=alpha, k=1e-3, h=(0.0, 0.0, H))
+    _, x, info = O.step_euler(g, prm, O.Opts(rtol=1e-13), m)
+    m0 = m[:, 0, 0]
+    h = np.array([0, 0, H])
+    ref = -np.cross(m0, h) - alpha * np.cross(m0, np.cross(m0, h))
+    assert np.allclose(x[:3, 0, 0], ref, atol=1e-12)
+    assert np.allclose(x[:3], x[:3, :1, :1], atol=1e-13)
+
+
+@pytest.mark.parametrize("scheme,order", [("euler", 1.0), ("midpoint", 2.0)])
+def test_temporal_order_uniform_field(scheme, order):
+    g = O.Grid((2, 2))
+    H, alpha, T = 1.0, 0.3, 1.0
+    errs = []
+    for nsteps in (10, 20, 40):
+        k = T / nsteps
+        prm = O.Params(alpha=alpha, k=k, h=(0.0, 0.0, H))
+        m = _uniform(1.2, 0.1, g.shape)
+        vprev = None
+        for _ in range(nsteps):
+            if scheme == "euler":
+                m, x, _ = O.step_euler(g, prm, O.Opts(rtol=1e-14), m)
+            else:
+                m, x, _ = O.step_midpoint(g, prm, O.Opts(rtol=1e-14, picard_tol=1e-14), m, vprev)
+                vprev = x[:3]
+        errs.append(np.abs(m[:, 0, 0] - _exact_uniform(1.2, 0.1, H, alpha, T)).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(rates - order) < 0.1), (errs, rates)
+
+
+# ------------------------------------------------------------------ midpoint invariants (Sec. 3.3)
+
+def test_midpoint_length_and_exact_dissipation():
+    """Exact solves: |m^{n+1}_j| = |m^n_j| and g(m^{n+1}) - g(m^n) = -alpha k/(1+alpha^2) ||v||^2_N
+    for the quadratic-affine exchange + Zeeman energy (Prop. nodal constraint and energy law)."""
+    g = O.Grid((8, 8))
+    m = I.smooth2d(g.n, seed=18)
+    prm = O.Params(alpha=0.1, k=4e-3, h=(0.0, 0.0, 0.5))
+    opts = O.Opts(use_dense=1, picard_tol=1e-15, picard_max=200)
+    mn, x, info = O.step_midpoint(g, prm, opts, m)
+    assert info.picard_iters >= 2
+    drift = np.abs(np.sqrt(np.sum(mn * mn, 0)) - np.sqrt(np.sum(m * m, 0))).max()
+    assert drift <= 1e-13
+    e0, e1 = O.energy(g, prm, m), O.energy(g, prm, mn)
+    v2 = np.mean(np.sum(x[:3] ** 2, axis=0))
+    resid = e1 - e0 + prm.alpha * prm.k / (1 + prm.alpha ** 2) * v2
+    assert abs(resid) <= 1e-13 * max(1.0, abs(e0))
+    assert e1 < e0
+
+
+def test_energy_pins_3d_micromagnetic():
+    """Initial energy 1.8083333333 and energy after 10 midpoint steps 1.7619940172 (N = 16),
+    exchange + periodic demag + anisotropy + Zeeman (Sec. 4.6)."""
+    G = GOLD["energy3d"]
+    N = G["N"]
+    g = O.Grid((N, N, N), (2 * np.pi,) * 3)
+    prm = O.Params(alpha=0.2, k=G["k"], lam=0.5, h=tuple(G["h"]), k_an=G["k_an"],
+                   e_an=(0.0, 0.0, 1.0), demag=1)
+    m = I.energy3d(g.n)
+    assert abs(O.energy(g, prm, m) - G["initial"]["value"]) <= G["initial"]["tol"]
+    O.set_transform(O.FFT)
+    try:
+        ms, xs, infos = O.run_midpoint(g, prm, O.Opts(rtol=1e-11, picard_tol=1e-11, restart=50),
+                                       m, G["steps"])
+    finally:
+        O.set_transform(O.DFT)
+    es = [O.energy(g, prm, mm) for mm in ms]
+    assert all(b < a for a, b in zip(es[:-1], es[1:]))       # monotone decay
+    assert abs(es[-1] - G["final"]["value"]) <= G["final"]["tol"], es[-1]
+    drift = max(np.abs(np.sqrt(np.sum(mm * mm, 0)) - 1).max() for mm in ms)
+    assert drift <= 1e-10
+
+
+# ------------------------------------------------------------------ adjoint vs central finite differences
+
+def test_adjoint_matches_central_differences():
+    g = O.Grid((4, 4))
+    m0 = I.smooth2d(g.n, seed=19, noise=0.05)
+    tgt = I.smooth2d(g.n, seed=20, noise=0.3)
+    prm = O.Params(alpha=0.1, k=2e-3, h=(0.1, -0.2, 0.5))
+    opts = O.Opts(use_dense=1, picard_tol=1e-15, picard_max=200)
+    nsteps = 3
+    loss, da, dh, dm0, _ = O.midpoint_loss_grad(g, prm, opts, m0, tgt, nsteps)
+
+    def L(prm_, m0_):
+        ms, _, _ = O.run_midpoint(g, prm_, opts, m0_, nsteps)
+        return 0.5 * float(np.sum((ms[-1] - tgt) ** 2))
+
+    eps = 1e-6
+    import dataclasses
+    fd_a = (L(dataclasses.replace(prm, alpha=prm.alpha + eps), m0)
+            - L(dataclasses.replace(prm, alpha=prm.alpha - eps), m0)) / (2 * eps)
+    assert abs(fd_a - da) <= 1e-6 * max(abs(da), 1e-3)
+    for c in range(3):
+        hp = list(prm.h); hm = list(prm.h)
+        hp[c] += eps; hm[c] -= eps
+        fd = (L(dataclasses.replace(prm, h=tuple(hp)), m0) - L(dataclasses.replace(prm, h=tuple(hm)), m0)) / (2 * eps)
+        assert abs(fd - dh[c]) <= 1e-6 * max(abs(dh[c]), 1e-3)
+    d = np.random.default_rng(21).standard_normal(m0.shape)
+    fd = (L(prm, m0 + eps * d) - L(prm, m0 - eps * d)) / (2 * eps)
+    assert abs(fd - np.sum(dm0 * d)) <= 1e-6 * max(abs(fd), 1e-3)
