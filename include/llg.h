@@ -1,0 +1,168 @@
+/*
+ * llg.h -- C ABI of the B300 (sm_103a) FFT--HSS preconditioned GMRES library
+ * for the periodic tangent-plane Landau--Lifshitz--Gilbert saddle system.
+ *
+ * Problem (paper Sec. 2.4, eqs. "total system 2" and "saddle point system";
+ * Sec. 3.3, eq. "C-N"): on a periodic grid with N_g nodes, find the velocity
+ * v (3 components per node) and multiplier r (1 per node) with
+ *
+ *   [ A(m)  B(m)^T ] [v]   [f]      A = alpha I + theta k Chat (-Lap_N) + [m]x,
+ *   [ -B(m)   0    ] [r] = [0],     B v = (m_i . v_i)_i,  Chat = (1 + alpha^2) c_ex.
+ *
+ * The second block row is negated as in the paper; the solution is the same.
+ *
+ * Memory layout (all calls): structure-of-arrays planes, node index
+ * j = ix + n0 * (iy + n1 * iz) (x fastest).  m has 3 planes (m1|m2|m3);
+ * a saddle vector x has 4 planes (v1|v2|v3|r).  Every array argument is a
+ * caller-owned DEVICE pointer (cudaMalloc or torch) on the device current when
+ * the context was created, unless stated otherwise; inputs and outputs must not
+ * alias.  Pointers must be 16-byte aligned.
+ *
+ * Execution: every call is enqueued on the context's stream.  Calls that
+ * return an llg_info (solves, steps, adjoint) synchronise that stream before
+ * returning; the others are asynchronous.  Argument errors are detected on the
+ * host before any launch.  A context is not thread-safe: one context per
+ * stream.  Errors are returned as status codes; llg_last_error() gives text.
+ */
+#ifndef LLG_H
+#define LLG_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LLG_OK = 0,
+    LLG_ERR_INVALID_ARG = 1,      /* null pointer, bad parameter value */
+    LLG_ERR_UNSUPPORTED_SIZE = 2, /* grid axis not a power of two in [2, 1024] */
+    LLG_ERR_NOT_CONVERGED = 3,    /* iteration cap reached; outputs hold the last iterate */
+    LLG_ERR_BREAKDOWN = 4,        /* non-finite residual in GMRES */
+    LLG_ERR_DEGENERATE_NODE = 5,  /* |m_i| = 0 at some node: the saddle matrix is singular */
+    LLG_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
+    LLG_ERR_OOM = 7,              /* device allocation failed */
+    LLG_ERR_CUDA = 8              /* CUDA runtime error */
+} llg_status;
+
+enum { LLG_EX_SPECTRAL = 0, LLG_EX_FD2 = 1 };
+/* precision of a solve: all FP64 (left-preconditioned GMRES on M^{-1}A), or flexible GMRES
+   with the FFT--HSS application and its inner matvec in FP32 (Arnoldi, least squares,
+   true residual and the solution update stay FP64) */
+enum { LLG_PREC_FP64 = 0, LLG_PREC_FP32_FLEX = 1 };
+
+typedef struct llg_ctx llg_ctx;
+
+/* periodic cell prod_l (0, L_l); n[l] points per axis, a power of two in [2, 1024];
+   dim = 2 uses n[0], n[1] (n[2] ignored) */
+typedef struct {
+    int dim;
+    int n[3];
+    double L[3];
+} llg_grid;
+
+/* alpha > 0 damping; c_ex > 0 normalised exchange coefficient (paper: 1);
+   k >= 0 time step; theta in {1, 1/2} (Euler / midpoint; steps set it themselves);
+   lambda > 0 HSS shift; h_ext uniform applied field; exchange = LLG_EX_* */
+typedef struct {
+    double alpha, c_ex, k, theta, lambda;
+    double h_ext[3];
+    int exchange;
+} llg_params;
+
+typedef struct {
+    int restart;        /* GMRES restart length, 1..64 */
+    int max_iters;      /* cap on total Arnoldi steps per solve */
+    double rtol;        /* stop when ||b - A x|| <= rtol ||b|| (true residual, FP64) */
+    int precision;      /* LLG_PREC_* */
+    int picard_max;     /* midpoint: cap on Picard iterations */
+    double picard_tol;  /* midpoint: stop when ||v^p - v^{p-1}|| <= picard_tol ||v^p|| */
+    int diagnostics;    /* steps: 1 = also compute energies and the dissipation residual */
+} llg_opts;
+
+typedef struct {
+    int iters;                    /* Arnoldi steps (all cycles, all Picard iterations) */
+    int restarts;                 /* GMRES cycles */
+    int picard_iters;             /* linear solves in a midpoint step */
+    int applies;                  /* FFT--HSS applications (fused operator counts one) */
+    double rel_res_true;          /* final ||b - A x|| / ||b|| (worst over Picard solves) */
+    double max_len_drift;         /* steps: max_i | |m^{n+1}_i| - |m^n_i| | */
+    double energy_before, energy_after;   /* diagnostics: volume-averaged exchange + Zeeman energy */
+    double dissipation_residual;  /* g(m^{n+1}) - g(m^n) + alpha k/(1+alpha^2) ||v||_N^2 (volume avg) */
+    int status;                   /* llg_status of the call */
+} llg_info;
+
+/* Create a context for one grid; cuda_stream is a cudaStream_t (NULL = legacy default stream).
+   Allocates twiddle/symbol tables and spectral scratch on the current device.
+   Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA. */
+llg_status llg_create(const llg_grid *grid, void *cuda_stream, llg_ctx **out);
+/* Free every device and host resource of the context (synchronises its stream). */
+llg_status llg_destroy(llg_ctx *ctx);
+/* Text of the last error on this context (never NULL; empty after success). */
+const char *llg_last_error(const llg_ctx *ctx);
+/* Re-target the context at another stream of the same device. */
+llg_status llg_set_stream(llg_ctx *ctx, void *cuda_stream);
+/* Number of kernels this context has launched so far (for launch accounting). */
+long long llg_launch_count(const llg_ctx *ctx);
+/* Nodes of the context's grid. */
+long long llg_nodes(const llg_ctx *ctx);
+
+/* Saddle matvec y = A x, or y = A^T x when transpose != 0 (Sec. 2.4 eq. "saddle point
+   system"; Sec. 3.2: the forward action uses the Fourier symbol without inversion plus the
+   nodal formulas of eqs. (S), (Lambda)).  m: 3 planes; x, y: 4 planes; FP64. */
+llg_status llg_saddle_apply(llg_ctx *ctx, const llg_params *prm, const double *m, const double *x,
+                            double *y, int transpose);
+
+/* FFT--HSS preconditioner z = M^{-1} p with M = (H + lambda I)(S + lambda I) (Sec. 3.2):
+   Algorithm 1 (Fourier solve of the shifted exchange block, multiplier / lambda) followed by
+   the closed-form 4x4 nodal inverse, eq. (inverse S).  transpose != 0 applies
+   M^{-T} = (H + lambda I)^{-1} (S + lambda I)^{-T}.  FP64. */
+llg_status llg_ffthss_apply(llg_ctx *ctx, const llg_params *prm, const double *m, const double *p,
+                            double *z, int transpose);
+/* The same in FP32 (m, p, z float planes). */
+llg_status llg_ffthss_apply_f32(llg_ctx *ctx, const llg_params *prm, const float *m, const float *p,
+                                float *z, int transpose);
+/* Left-preconditioned operator z = M^{-1} A x in one Fourier round trip, using
+   (H + lambda I)^{-1} A = I + (H + lambda I)^{-1}(S - lambda I) (consequence of Sec. 3.2's
+   splitting; the operator GMRES iterates on).  FP64. */
+llg_status llg_precond_saddle_apply(llg_ctx *ctx, const llg_params *prm, const double *m,
+                                    const double *x, double *z);
+
+/* Solve A(m) x = b by FFT--HSS preconditioned GMRES(restart) (Sec. 3.2, Sec. 4.1).
+   x: on entry the initial guess, on exit the solution.  Precision per opts->precision.
+   Convergence is declared on the FP64 true residual.  Returns NOT_CONVERGED (x holds the
+   last iterate) when max_iters is reached; DEGENERATE_NODE if some |m_i| = 0. */
+llg_status llg_gmres_solve(llg_ctx *ctx, const llg_params *prm, const llg_opts *opts,
+                           const double *m, const double *b, double *x, llg_info *info);
+
+/* Projected implicit Euler tangent-plane step (Sec. 2.4 eq. "total system", Sec. 3.2):
+   f = Chat Lap_N m^n + (1 + alpha^2) h_ext; solve with theta = 1 and blocks from m^n;
+   m^{n+1}_i = (m^n_i + k v_i) / |m^n_i + k v_i|.  x_out receives (v | r). */
+llg_status llg_step_euler(llg_ctx *ctx, const llg_params *prm, const llg_opts *opts,
+                          const double *m_n, double *m_next, double *x_out, llg_info *info);
+
+/* Crank--Nicolson-type midpoint step with Picard iteration (Sec. 3.3 eqs. "C-N", "hatm"):
+   mhat^0 = m^n + (k/2) v_prev (v_prev may be NULL: zero); each Picard step solves the
+   saddle system with theta = 1/2 and blocks from mhat^p; mhat^{p+1} = m^n + (k/2) v^p;
+   m^{n+1} = m^n + k v.  x_out receives (v^{n+1/2} | r) and also serves as the warm start. */
+llg_status llg_step_midpoint(llg_ctx *ctx, const llg_params *prm, const llg_opts *opts,
+                             const double *m_n, const double *v_prev, double *m_next,
+                             double *x_out, llg_info *info);
+
+/* Adjoint of one converged midpoint step (derived from Sec. 3.3 eqs. "C-N", "hatm"; the paper
+   has no adjoint): with R(v, r; m^n, alpha, h) = 0 the step's residual and J its Jacobian in
+   (v, r), solves J^T y = (k mbar_next, 0) by GMRES preconditioned with M(mhat)^{-T}, then
+   mbar_n = mbar_next - (dR/dm^n)^T y, *dalpha -= y^T dR/dalpha, dh[c] -= y^T dR/dh_c.
+   m_n: 3 planes; x: the step's (v | r) (4 planes); mbar_next, mbar_n: 3 planes (device).
+   dalpha, dh: HOST pointers, accumulated (+=).  Uniform applied field only. FP64. */
+llg_status llg_adjoint_step(llg_ctx *ctx, const llg_params *prm, const llg_opts *opts,
+                            const double *m_n, const double *x, const double *mbar_next,
+                            double *mbar_n, double *dalpha, double dh[3], llg_info *info);
+
+/* Volume-averaged exchange + Zeeman energy g_N(m) = (1/N_g) sum_j [c_ex/2 m.(-Lap_N m) - h.m]
+   (Sec. 2.1; the quadratic-affine energy of Prop. "nodal constraint and energy law").
+   *out is a HOST pointer; synchronises the stream. */
+llg_status llg_energy(llg_ctx *ctx, const llg_params *prm, const double *m, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,220 @@
+"""B300-native FFT--HSS preconditioned GMRES for the periodic tangent-plane LLG
+saddle system (arXiv 2607.15290).
+
+Thin Python binding of the C ABI in ``include/llg.h``: every function here
+only checks shapes/dtypes, allocates output tensors (PyTorch is used for device
+memory and streams) and forwards raw device pointers to the CUDA library.  All
+arithmetic of the method runs in the library's kernels; if the library is
+missing the calls raise, there is no CPU fallback.
+
+Array conventions: ``m`` is (3, *grid_shape) and saddle vectors ``x = (v, r)``
+are (4, *grid_shape), float64 CUDA tensors, grid_shape = (n1, n0) in 2D or
+(n2, n1, n0) in 3D (x fastest), matching the node index j = i0 + n0 (i1 + n1 i2).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+from . import _abi
+from ._abi import EX_FD2, EX_SPECTRAL, PREC_FP32_FLEX, PREC_FP64
+
+__all__ = [
+    "LLGError", "Params", "Opts", "Context", "EX_SPECTRAL", "EX_FD2", "PREC_FP64", "PREC_FP32_FLEX",
+    "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_precond_saddle_apply",
+    "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy",
+]
+
+
+class LLGError(RuntimeError):
+    def __init__(self, status, msg, info=None):
+        super().__init__(f"{_abi.STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.info = info
+
+
+@dataclass
+class Params:
+    alpha: float = 0.2
+    c_ex: float = 1.0
+    k: float = 1e-2
+    theta: float = 1.0
+    lam: float = 0.5
+    h_ext: tuple = (0.0, 0.0, 0.0)
+    exchange: int = EX_SPECTRAL
+
+    def c(self):
+        p = _abi.Params()
+        p.alpha, p.c_ex, p.k, p.theta, p.lam = self.alpha, self.c_ex, self.k, self.theta, self.lam
+        for i in range(3):
+            p.h_ext[i] = self.h_ext[i]
+        p.exchange = self.exchange
+        return p
+
+
+@dataclass
+class Opts:
+    restart: int = 30
+    max_iters: int = 3000
+    rtol: float = 1e-10
+    precision: int = PREC_FP64
+    picard_max: int = 50
+    picard_tol: float = 1e-10
+    diagnostics: int = 0
+
+    def c(self):
+        o = _abi.Opts()
+        o.restart, o.max_iters, o.rtol, o.precision = self.restart, self.max_iters, self.rtol, self.precision
+        o.picard_max, o.picard_tol, o.diagnostics = self.picard_max, self.picard_tol, self.diagnostics
+        return o
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """Owns an ``llg_ctx`` for one periodic grid on the current CUDA device/stream."""
+
+    def __init__(self, n, L=None, stream=None):
+        torch = _torch()
+        self.lib = _abi.lib()
+        self.n = tuple(int(v) for v in n)
+        self.L = tuple(float(v) for v in (L if L is not None else (1.0,) * len(self.n)))
+        g = _abi.Grid()
+        g.dim = len(self.n)
+        for i in range(3):
+            g.n[i] = self.n[i] if i < g.dim else 1
+            g.L[i] = self.L[i] if i < g.dim else 1.0
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = self.lib.llg_create(C.byref(g), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise LLGError(st, "llg_create failed")
+        self.h = h
+
+    @property
+    def shape(self):
+        return tuple(reversed(self.n))
+
+    @property
+    def nodes(self):
+        return int(self.lib.llg_nodes(self.h))
+
+    def launches(self):
+        return int(self.lib.llg_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.llg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ marshalling helpers
+    def _check(self, st, info=None):
+        if st != 0:
+            raise LLGError(st, self.lib.llg_last_error(self.h).decode(), info)
+
+    def _arr(self, t, comps, dtype=None):
+        torch = _torch()
+        dtype = dtype or torch.float64
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+            raise ValueError(f"expected a contiguous {dtype} CUDA tensor")
+        if tuple(t.shape) != (comps,) + self.shape:
+            raise ValueError(f"expected shape {(comps,) + self.shape}, got {tuple(t.shape)}")
+        return C.c_void_p(t.data_ptr())
+
+    def empty(self, comps, dtype=None):
+        torch = _torch()
+        return torch.empty((comps,) + self.shape, dtype=dtype or torch.float64, device="cuda")
+
+
+def llg_saddle_apply(ctx: Context, prm: Params, m, x, transpose=False, out=None):
+    y = out if out is not None else ctx.empty(4)
+    ctx._check(ctx.lib.llg_saddle_apply(ctx.h, C.byref(prm.c()), ctx._arr(m, 3), ctx._arr(x, 4), ctx._arr(y, 4),
+                                        int(transpose)))
+    return y
+
+
+def llg_ffthss_apply(ctx: Context, prm: Params, m, p, transpose=False, out=None):
+    z = out if out is not None else ctx.empty(4)
+    ctx._check(ctx.lib.llg_ffthss_apply(ctx.h, C.byref(prm.c()), ctx._arr(m, 3), ctx._arr(p, 4), ctx._arr(z, 4),
+                                        int(transpose)))
+    return z
+
+
+def llg_ffthss_apply_f32(ctx: Context, prm: Params, m, p, transpose=False, out=None):
+    torch = _torch()
+    z = out if out is not None else ctx.empty(4, torch.float32)
+    ctx._check(ctx.lib.llg_ffthss_apply_f32(ctx.h, C.byref(prm.c()), ctx._arr(m, 3, torch.float32),
+                                            ctx._arr(p, 4, torch.float32), ctx._arr(z, 4, torch.float32),
+                                            int(transpose)))
+    return z
+
+
+def llg_precond_saddle_apply(ctx: Context, prm: Params, m, x, out=None):
+    z = out if out is not None else ctx.empty(4)
+    ctx._check(ctx.lib.llg_precond_saddle_apply(ctx.h, C.byref(prm.c()), ctx._arr(m, 3), ctx._arr(x, 4),
+                                                ctx._arr(z, 4)))
+    return z
+
+
+def llg_gmres_solve(ctx: Context, prm: Params, opts: Opts, m, b, x=None, raise_on_error=True):
+    """Returns (x, info dict); x is the solution (the initial guess is zeros unless given)."""
+    if x is None:
+        x = ctx.empty(4)
+        x.zero_()
+    info = _abi.Info()
+    st = ctx.lib.llg_gmres_solve(ctx.h, C.byref(prm.c()), C.byref(opts.c()), ctx._arr(m, 3), ctx._arr(b, 4),
+                                 ctx._arr(x, 4), C.byref(info))
+    if raise_on_error:
+        ctx._check(st, info.as_dict())
+    return x, info.as_dict()
+
+
+def llg_step_euler(ctx: Context, prm: Params, opts: Opts, m, m_next=None, x_out=None, raise_on_error=True):
+    m_next = m_next if m_next is not None else ctx.empty(3)
+    x_out = x_out if x_out is not None else ctx.empty(4)
+    info = _abi.Info()
+    st = ctx.lib.llg_step_euler(ctx.h, C.byref(prm.c()), C.byref(opts.c()), ctx._arr(m, 3), ctx._arr(m_next, 3),
+                                ctx._arr(x_out, 4), C.byref(info))
+    if raise_on_error:
+        ctx._check(st, info.as_dict())
+    return m_next, x_out, info.as_dict()
+
+
+def llg_step_midpoint(ctx: Context, prm: Params, opts: Opts, m, v_prev=None, m_next=None, x_out=None,
+                      raise_on_error=True):
+    m_next = m_next if m_next is not None else ctx.empty(3)
+    x_out = x_out if x_out is not None else ctx.empty(4)
+    vp = C.c_void_p(0) if v_prev is None else ctx._arr(v_prev, 3)
+    info = _abi.Info()
+    st = ctx.lib.llg_step_midpoint(ctx.h, C.byref(prm.c()), C.byref(opts.c()), ctx._arr(m, 3), vp,
+                                   ctx._arr(m_next, 3), ctx._arr(x_out, 4), C.byref(info))
+    if raise_on_error:
+        ctx._check(st, info.as_dict())
+    return m_next, x_out, info.as_dict()
+
+
+def llg_adjoint_step(ctx: Context, prm: Params, opts: Opts, m_n, x, mbar_next, mbar_n=None):
+    """Returns (mbar_n, dL/dalpha contribution, dL/dh contribution (3,), info)."""
+    mbar_n = mbar_n if mbar_n is not None else ctx.empty(3)
+    da = C.c_double(0.0)
+    dh = (C.c_double * 3)(0.0, 0.0, 0.0)
+    info = _abi.Info()
+    st = ctx.lib.llg_adjoint_step(ctx.h, C.byref(prm.c()), C.byref(opts.c()), ctx._arr(m_n, 3), ctx._arr(x, 4),
+                                  ctx._arr(mbar_next, 3), ctx._arr(mbar_n, 3), C.byref(da), dh, C.byref(info))
+    ctx._check(st, info.as_dict())
+    return mbar_n, da.value, [dh[0], dh[1], dh[2]], info.as_dict()
+
+
+def llg_energy(ctx: Context, prm: Params, m):
+    out = C.c_double(0.0)
+    ctx._check(ctx.lib.llg_energy(ctx.h, C.byref(prm.c()), ctx._arr(m, 3), C.byref(out)))
+    return out.value

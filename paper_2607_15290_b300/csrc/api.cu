@@ -1,0 +1,710 @@
+// api.cu -- the C ABI of include/llg.h: context, operators, solves, time steps,
+// adjoint.  Host code here only validates arguments, sequences kernels on the
+// context's stream and reads back convergence scalars; all arithmetic of the
+// method runs in the kernels of spectral.cu, krylov.cu and below.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+#include <algorithm>
+#include "llg_internal.h"
+#include "krylov.h"
+#include "reduce.cuh"
+
+using namespace llg;
+
+namespace llg {
+
+llg_status set_error(llg_ctx *c, llg_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+llg_status cuda_check(llg_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LLG_OK;
+    cudaGetLastError();
+    return set_error(c, e == cudaErrorMemoryAllocation ? LLG_ERR_OOM : LLG_ERR_CUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ small kernels
+
+__global__ void k_min_norm2(const double *__restrict__ m, long long N, double *partials) {
+    long long lo, hi;
+    block_chunk(N, lo, hi);
+    double v = -1e300;
+    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+        const double a = m[j], b = m[N + j], c = m[2 * N + j];
+        v = fmax(v, -(a * a + b * b + c * c));
+    }
+    block_max_store(v, partials + (long long)blockIdx.x * RB_STRIDE);
+}
+
+__global__ void k_max_partials(const double *__restrict__ partials, int nb, double *dst) {
+    if (threadIdx.x != 0) return;
+    double s = -1e300;
+    for (int b = 0; b < nb; ++b) s = fmax(s, partials[(long long)b * RB_STRIDE]);
+    *dst = s;
+}
+
+__global__ void k_sum_partials_n(const double *__restrict__ partials, int nb, int cnt, double *dst) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += partials[(long long)b * RB_STRIDE + i];
+        dst[i] = s;
+    }
+}
+
+__global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, long long n) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        b[e] = (float)a[e];
+}
+
+// m^{n+1} = (m + k v) / |m + k v|, and max_i | |m^{n+1}_i| - |m^n_i| |
+__global__ void k_euler_update(const double *__restrict__ m, const double *__restrict__ v, double k, double *mn,
+                               long long N, double *partials) {
+    long long lo, hi;
+    block_chunk(N, lo, hi);
+    double drift = 0.0;
+    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+        const double a = m[j] + k * v[j], b = m[N + j] + k * v[N + j], c = m[2 * N + j] + k * v[2 * N + j];
+        const double s = sqrt(a * a + b * b + c * c);
+        mn[j] = a / s;
+        mn[N + j] = b / s;
+        mn[2 * N + j] = c / s;
+        const double m0 = sqrt(m[j] * m[j] + m[N + j] * m[N + j] + m[2 * N + j] * m[2 * N + j]);
+        drift = fmax(drift, fabs(1.0 - m0));
+    }
+    block_max_store(drift, partials + (long long)blockIdx.x * RB_STRIDE);
+}
+
+// out = m + c v (3 planes; v may be NULL)
+__global__ void k_axpy3(const double *__restrict__ m, const double *__restrict__ v, double c, double *out, long long n3) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x)
+        out[e] = m[e] + (v ? c * v[e] : 0.0);
+}
+
+// partial sums of |v - vold|^2 and |v|^2
+__global__ void k_picard_norms(const double *__restrict__ v, const double *__restrict__ vold, long long n3, double *partials) {
+    long long lo, hi;
+    block_chunk(n3, lo, hi);
+    double acc[2] = {0.0, 0.0};
+    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        const double d = v[e] - vold[e];
+        acc[0] += d * d;
+        acc[1] += v[e] * v[e];
+    }
+    block_reduce_store<2>(acc, 2, partials + (long long)blockIdx.x * RB_STRIDE);
+}
+
+// m^{n+1} = m^n + k v and max_i | |m^{n+1}_i| - |m^n_i| |
+__global__ void k_mid_final(const double *__restrict__ m, const double *__restrict__ v, double k, double *mn,
+                            long long N, double *partials) {
+    long long lo, hi;
+    block_chunk(N, lo, hi);
+    double drift = 0.0;
+    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+        const double a0 = m[j], b0 = m[N + j], c0 = m[2 * N + j];
+        const double a = a0 + k * v[j], b = b0 + k * v[N + j], c = c0 + k * v[2 * N + j];
+        mn[j] = a;
+        mn[N + j] = b;
+        mn[2 * N + j] = c;
+        drift = fmax(drift, fabs(sqrt(a * a + b * b + c * c) - sqrt(a0 * a0 + b0 * b0 + c0 * c0)));
+    }
+    block_max_store(drift, partials + (long long)blockIdx.x * RB_STRIDE);
+}
+
+// energy density sum: m . T - h . m, with T = (c_ex/2)(-Lap) m
+__global__ void k_energy_partials(const double *__restrict__ m, const double *__restrict__ T, double h0, double h1,
+                                  double h2, long long N, double *partials) {
+    long long lo, hi;
+    block_chunk(N, lo, hi);
+    double acc[1] = {0.0};
+    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+        const double a = m[j], b = m[N + j], c = m[2 * N + j];
+        acc[0] += a * T[j] + b * T[N + j] + c * T[2 * N + j] - (h0 * a + h1 * b + h2 * c);
+    }
+    block_reduce_store<1>(acc, 1, partials + (long long)blockIdx.x * RB_STRIDE);
+}
+
+// adjoint preparation: mhat = m + (k/2) v; rhs = (k mbar, 0); u = alpha c_ex (k v + 2 m)
+__global__ void k_adj_prep(const double *__restrict__ m, const double *__restrict__ v, const double *__restrict__ mbar,
+                           double k, double ac, double *mhat, double *rhs, double *u, long long N) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        for (int q = 0; q < 3; ++q) {
+            const long long e = q * N + j;
+            mhat[e] = m[e] + 0.5 * k * v[e];
+            rhs[e] = k * mbar[e];
+            u[e] = ac * (k * v[e] + 2.0 * m[e]);
+        }
+        rhs[3 * N + j] = 0.0;
+    }
+}
+
+// mbar_n = mbar_next - [Chat(-Lap) y_v + v x y_v + r y_v - v y_r];
+// partial sums of -y_v . (v + (-Lap) u - 2 alpha h) and of y_v (per component)
+__global__ void k_adj_final(const double *__restrict__ mbar_next, const double *__restrict__ y,
+                            const double *__restrict__ lapy, const double *__restrict__ xf,
+                            const double *__restrict__ lapu, double alpha, double h0, double h1, double h2,
+                            double *mbar_n, long long N, double *partials) {
+    long long lo, hi;
+    block_chunk(N, lo, hi);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const double h[3] = {h0, h1, h2};
+    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+        const double y1 = y[j], y2 = y[N + j], y3 = y[2 * N + j], yr = y[3 * N + j];
+        const double v1 = xf[j], v2 = xf[N + j], v3 = xf[2 * N + j], r = xf[3 * N + j];
+        const double cx[3] = {v2 * y3 - v3 * y2, v3 * y1 - v1 * y3, v1 * y2 - v2 * y1};
+        const double yv[3] = {y1, y2, y3}, vv[3] = {v1, v2, v3};
+        for (int q = 0; q < 3; ++q) {
+            const long long e = q * N + j;
+            mbar_n[e] = mbar_next[e] - (lapy[e] + cx[q] + r * yv[q] - vv[q] * yr);
+            acc[0] -= yv[q] * (vv[q] + lapu[e] - 2.0 * alpha * h[q]);
+            acc[1 + q] += yv[q];
+        }
+    }
+    block_reduce_store<4>(acc, 4, partials + (long long)blockIdx.x * RB_STRIDE);
+}
+
+}  // namespace llg
+
+// ------------------------------------------------------------------ helpers
+
+namespace {
+
+bool is_pow2(int n) { return n >= 2 && n <= 1024 && (n & (n - 1)) == 0; }
+int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+double chat(const llg_params *p) { return (1.0 + p->alpha * p->alpha) * p->c_ex; }
+
+llg_status check_params(llg_ctx *c, const llg_params *p) {
+    if (!p) return set_error(c, LLG_ERR_INVALID_ARG, "params is NULL");
+    const double v[] = {p->alpha, p->c_ex, p->k, p->theta, p->lambda, p->h_ext[0], p->h_ext[1], p->h_ext[2]};
+    for (double d : v)
+        if (!std::isfinite(d)) return set_error(c, LLG_ERR_INVALID_ARG, "non-finite parameter");
+    if (!(p->alpha > 0) || !(p->c_ex > 0) || !(p->lambda > 0) || p->k < 0 || !(p->theta > 0))
+        return set_error(c, LLG_ERR_INVALID_ARG, "need alpha > 0, c_ex > 0, lambda > 0, k >= 0, theta > 0");
+    if (p->exchange != LLG_EX_SPECTRAL && p->exchange != LLG_EX_FD2)
+        return set_error(c, LLG_ERR_INVALID_ARG, "unknown exchange discretisation");
+    return LLG_OK;
+}
+
+llg_status check_opts(llg_ctx *c, const llg_opts *o) {
+    if (!o) return set_error(c, LLG_ERR_INVALID_ARG, "opts is NULL");
+    if (o->restart < 1 || o->restart > GmresDev::MAXM) return set_error(c, LLG_ERR_INVALID_ARG, "restart must be in [1, 64]");
+    if (o->max_iters < 1 || !(o->rtol > 0) || !std::isfinite(o->rtol))
+        return set_error(c, LLG_ERR_INVALID_ARG, "need max_iters >= 1 and rtol > 0");
+    if (o->precision != LLG_PREC_FP64 && o->precision != LLG_PREC_FP32_FLEX)
+        return set_error(c, LLG_ERR_INVALID_ARG, "unknown precision");
+    if (o->picard_max < 1 || !(o->picard_tol > 0)) return set_error(c, LLG_ERR_INVALID_ARG, "need picard_max >= 1 and picard_tol > 0");
+    return LLG_OK;
+}
+
+llg_status ensure_spec(llg_ctx *c, bool fp64, bool fp32) {
+    const size_t elems = (size_t)c->geo.rows * c->geo.S;
+    if (fp64 && !c->spec64) {
+        cudaError_t e = cudaMalloc(&c->spec64, elems * sizeof(double2));
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->spec64, 0, elems * sizeof(double2), c->stream);
+        if (e != cudaSuccess) { c->spec64 = nullptr; return cuda_check(c, e, "spectral buffer (FP64)"); }
+    }
+    if (fp32 && !c->spec32) {
+        cudaError_t e = cudaMalloc(&c->spec32, elems * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->spec32, 0, elems * sizeof(float2), c->stream);
+        if (e != cudaSuccess) { c->spec32 = nullptr; return cuda_check(c, e, "spectral buffer (FP32)"); }
+    }
+    return LLG_OK;
+}
+
+llg_status ensure_aux(llg_ctx *c) {
+    if (c->aux) return LLG_OK;
+    cudaError_t e = cudaMalloc(&c->aux, sizeof(double) * 24 * c->geo.N);
+    if (e != cudaSuccess) { c->aux = nullptr; return cuda_check(c, e, "stepper scratch"); }
+    return LLG_OK;
+}
+
+llg_status ensure_m32(llg_ctx *c) {
+    if (c->m32) return LLG_OK;
+    cudaError_t e = cudaMalloc(&c->m32, sizeof(float) * 3 * c->geo.N);
+    if (e != cudaSuccess) { c->m32 = nullptr; return cuda_check(c, e, "FP32 field copy"); }
+    return LLG_OK;
+}
+
+int grid_blocks(llg_ctx *c) { return 4 * c->sm_count; }
+
+llg_status sync_scalars(llg_ctx *c, int count) {
+    cudaError_t e = cudaMemcpyAsync(c->hsc, c->dsc, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "device->host scalars");
+}
+
+template <typename TIn, typename TOut, typename T>
+NodalIO<TIn, TOut, T> make_io(const T *m, const TIn *x, TOut *y, const double *scale, double lam) {
+    NodalIO<TIn, TOut, T> io;
+    std::memset(&io, 0, sizeof(io));
+    io.m = m; io.x = x; io.y = y; io.scale = scale; io.lam = (T)lam;
+    return io;
+}
+
+Symbol sym_shifted_inverse(llg_ctx *c, const llg_params *p, double theta) {
+    return Symbol{p->alpha + p->lambda, theta * p->k * chat(p), 1.0 / (double)c->geo.N, 1, p->exchange};
+}
+Symbol sym_forward(llg_ctx *c, const llg_params *p, double theta) {
+    return Symbol{p->alpha, theta * p->k * chat(p), 1.0 / (double)c->geo.N, 0, p->exchange};
+}
+
+// FP64 operators ------------------------------------------------------------
+
+llg_status op_matvec64(llg_ctx *c, const llg_params *p, double theta, const double *m, const double *x,
+                       const double *scale, double *y, int transpose) {
+    auto io = make_io<double, double, double>(m, x, y, scale, p->lambda);
+    io.transpose = transpose;
+    return spectral_chain<double, double, double>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
+}
+
+llg_status op_apply64(llg_ctx *c, const llg_params *p, double theta, const double *m, const double *x,
+                      const double *scale, double *y, int transpose) {
+    auto io = make_io<double, double, double>(m, x, y, scale, p->lambda);
+    if (!transpose) return spectral_chain<double, double, double>(c, IN_V, OUT_APPLY, io, sym_shifted_inverse(c, p, theta));
+    return spectral_chain<double, double, double>(c, IN_NODAL_T, OUT_PLAIN, io, sym_shifted_inverse(c, p, theta));
+}
+
+llg_status op_fused64(llg_ctx *c, const llg_params *p, double theta, const double *m, const double *x,
+                      const double *scale, double *y) {
+    auto io = make_io<double, double, double>(m, x, y, scale, p->lambda);
+    return spectral_chain<double, double, double>(c, IN_FUSED, OUT_FUSED, io, sym_shifted_inverse(c, p, theta));
+}
+
+llg_status check_nodes(llg_ctx *c, const double *m) {
+    const int nb = reduction_blocks(c);
+    k_min_norm2<<<nb, RB_THREADS, 0, c->stream>>>(m, c->geo.N, c->red);
+    k_max_partials<<<1, 32, 0, c->stream>>>(c->red, nb, c->dsc);
+    c->launches += 2;
+    llg_status st = cuda_check(c, cudaGetLastError(), "node check");
+    if (st != LLG_OK) return st;
+    if ((st = sync_scalars(c, 1)) != LLG_OK) return st;
+    const double minn2 = -c->hsc[0];
+    if (!(minn2 > 0.0) || !std::isfinite(minn2))
+        return set_error(c, LLG_ERR_DEGENERATE_NODE, "some node has |m_i| = 0 (or non-finite): the saddle matrix is singular");
+    return LLG_OK;
+}
+
+// solve A(m; theta) x = b with the chosen precision
+llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *o, const double *m, const double *b,
+                 double *x, llg_info *info) {
+    llg_status st = check_nodes(c, m);
+    if (st != LLG_OK) return st;
+    const bool flex = o->precision == LLG_PREC_FP32_FLEX;
+    if ((st = ensure_spec(c, true, flex)) != LLG_OK) return st;
+    SolveOps ops;
+    ops.matvec = [=](const double *xx, double *yy) { return op_matvec64(c, p, theta, m, xx, nullptr, yy, 0); };
+    if (!flex) {
+        ops.prec = [=](const double *xx, const double *s, double *yy) { return op_apply64(c, p, theta, m, xx, s, yy, 0); };
+        ops.pop = [=](const double *xx, const double *s, double *yy) { return op_fused64(c, p, theta, m, xx, s, yy); };
+    } else {
+        if ((st = ensure_m32(c)) != LLG_OK) return st;
+        k_to_f32<<<grid_blocks(c), RB_THREADS, 0, c->stream>>>(m, c->m32, 3 * c->geo.N);
+        c->launches++;
+        const float *m32 = c->m32;
+        ops.fprec = [=](const double *xx, const double *s, float *zz) {
+            auto io = make_io<double, float, float>(m32, xx, zz, s, p->lambda);
+            return spectral_chain<float, double, float>(c, IN_V, OUT_APPLY, io, sym_shifted_inverse(c, p, theta));
+        };
+        ops.fmatvec = [=](const float *zz, double *ww) {
+            auto io = make_io<float, double, float>(m32, zz, ww, nullptr, p->lambda);
+            return spectral_chain<float, float, double>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
+        };
+    }
+    return gmres_run(c, ops, flex, o, b, x, info);
+}
+
+llg_status rhs_velocity(llg_ctx *c, const llg_params *p, const double *m, double *b) {
+    // f = Chat Lap_N m + (1 + alpha^2) h_ext ; multiplier row 0
+    auto io = make_io<double, double, double>(m, m, b, nullptr, p->lambda);
+    const double s = 1.0 + p->alpha * p->alpha;
+    io.fld[0] = s * p->h_ext[0];
+    io.fld[1] = s * p->h_ext[1];
+    io.fld[2] = s * p->h_ext[2];
+    Symbol sym{0.0, -chat(p), 1.0 / (double)c->geo.N, 0, p->exchange};
+    return spectral_chain<double, double, double>(c, IN_M, OUT_FIELD, io, sym);
+}
+
+llg_status energy_async(llg_ctx *c, const llg_params *p, const double *m, double *tmp, double *dst_dev) {
+    auto io = make_io<double, double, double>(m, m, tmp, nullptr, p->lambda);
+    Symbol sym{0.0, 0.5 * p->c_ex, 1.0 / (double)c->geo.N, 0, p->exchange};
+    llg_status st = spectral_chain<double, double, double>(c, IN_M, OUT_PLAIN, io, sym);
+    if (st != LLG_OK) return st;
+    const int nb = reduction_blocks(c);
+    k_energy_partials<<<nb, RB_THREADS, 0, c->stream>>>(m, tmp, p->h_ext[0], p->h_ext[1], p->h_ext[2], c->geo.N, c->red);
+    k_sum_partials_n<<<1, 32, 0, c->stream>>>(c->red, nb, 1, dst_dev);
+    c->launches += 2;
+    return cuda_check(c, cudaGetLastError(), "energy");
+}
+
+#define LLG_GUARD(ctx)                                                                       \
+    if (!(ctx)) return LLG_ERR_INVALID_ARG;                                                  \
+    (ctx)->err.clear();
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+llg_status llg_create(const llg_grid *grid, void *cuda_stream, llg_ctx **out) {
+    if (!out || !grid) return LLG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (grid->dim != 2 && grid->dim != 3) return LLG_ERR_INVALID_ARG;
+    for (int l = 0; l < grid->dim; ++l) {
+        if (!is_pow2(grid->n[l])) return LLG_ERR_UNSUPPORTED_SIZE;
+        if (!(grid->L[l] > 0) || !std::isfinite(grid->L[l])) return LLG_ERR_INVALID_ARG;
+    }
+    llg_ctx *c = new (std::nothrow) llg_ctx();
+    if (!c) return LLG_ERR_OOM;
+    c->grid = *grid;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    SpecGeom &g = c->geo;
+    g.dim = grid->dim;
+    for (int l = 0; l < 3; ++l) {
+        g.n[l] = l < grid->dim ? grid->n[l] : 1;
+        g.logn[l] = ilog2(g.n[l]);
+    }
+    g.N = (long long)g.n[0] * g.n[1] * g.n[2];
+    g.rows = (long long)g.n[1] * g.n[2];
+    g.S = ((g.n[0] + g.n[0] / 2 + 1) + 15) / 16 * 16;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    auto fail = [&](cudaError_t err, const char *what) {
+        llg_status s = cuda_check(c, err, what);
+        llg_destroy(c);
+        return s;
+    };
+    if (e != cudaSuccess) return fail(e, "device query");
+    // twiddle and symbol tables
+    for (int l = 0; l < 3; ++l) {
+        const int n = g.n[l];
+        std::vector<double2> t64(n);
+        std::vector<float2> t32(n);
+        std::vector<double> s64[2];
+        std::vector<float> s32[2];
+        for (int ex = 0; ex < 2; ++ex) { s64[ex].resize(n); s32[ex].resize(n); }
+        const long double twopi = 6.283185307179586476925286766559L;
+        for (int i = 0; i < n; ++i) {
+            const long double ang = twopi * (long double)i / (long double)n;
+            t64[i] = make_double2((double)cosl(ang), (double)-sinl(ang));
+            t32[i] = make_float2((float)cosl(ang), (float)-sinl(ang));
+            const int kw = i < n / 2 ? i : i - n;
+            double sp = 0.0, fd = 0.0;
+            if (l < grid->dim && n > 1) {
+                const long double xi = twopi * (long double)kw / (long double)grid->L[l];
+                sp = (double)(xi * xi);
+                const long double h = (long double)grid->L[l] / (long double)n;
+                const long double sn = sinl(3.14159265358979323846264338327950L * (long double)kw / (long double)n);
+                fd = (double)(4.0L / (h * h) * sn * sn);
+            }
+            s64[0][i] = sp; s64[1][i] = fd;
+            s32[0][i] = (float)sp; s32[1][i] = (float)fd;
+        }
+        if ((e = cudaMalloc(&c->tw64[l], sizeof(double2) * n)) != cudaSuccess) return fail(e, "tables");
+        if ((e = cudaMalloc(&c->tw32[l], sizeof(float2) * n)) != cudaSuccess) return fail(e, "tables");
+        cudaMemcpy(c->tw64[l], t64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
+        cudaMemcpy(c->tw32[l], t32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+        for (int ex = 0; ex < 2; ++ex) {
+            if ((e = cudaMalloc(&c->sig64[ex][l], sizeof(double) * n)) != cudaSuccess) return fail(e, "tables");
+            if ((e = cudaMalloc(&c->sig32[ex][l], sizeof(float) * n)) != cudaSuccess) return fail(e, "tables");
+            cudaMemcpy(c->sig64[ex][l], s64[ex].data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+            cudaMemcpy(c->sig32[ex][l], s32[ex].data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+        }
+    }
+    if ((e = cudaMalloc(&c->red, sizeof(double) * RB_STRIDE * reduction_blocks(c))) != cudaSuccess) return fail(e, "scratch");
+    if ((e = cudaMalloc(&c->dsc, sizeof(double) * 64)) != cudaSuccess) return fail(e, "scratch");
+    if ((e = cudaMallocHost(&c->hsc, sizeof(double) * 64)) != cudaSuccess) return fail(e, "pinned scratch");
+    if ((e = cudaMalloc(&c->gdev, sizeof(GmresDev))) != cudaSuccess) return fail(e, "GMRES state");
+    if ((e = cudaMemset(c->gdev, 0, sizeof(GmresDev))) != cudaSuccess) return fail(e, "GMRES state");
+    if ((e = cudaMallocHost(&c->ghost, sizeof(GmresDev))) != cudaSuccess) return fail(e, "pinned GMRES state");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "create");
+    *out = c;
+    return LLG_OK;
+}
+
+llg_status llg_destroy(llg_ctx *c) {
+    if (!c) return LLG_ERR_INVALID_ARG;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (int l = 0; l < 3; ++l) {
+        cudaFree(c->tw64[l]);
+        cudaFree(c->tw32[l]);
+        for (int ex = 0; ex < 2; ++ex) { cudaFree(c->sig64[ex][l]); cudaFree(c->sig32[ex][l]); }
+    }
+    cudaFree(c->spec64); cudaFree(c->spec32); cudaFree(c->red); cudaFree(c->dsc);
+    cudaFree(c->gdev); cudaFree(c->m32); cudaFree(c->aux);
+    if (c->hsc) cudaFreeHost(c->hsc);
+    if (c->ghost) cudaFreeHost(c->ghost);
+    Workspace &w = c->ws;
+    cudaFree(w.V); cudaFree(w.Z); cudaFree(w.W); cudaFree(w.T); cudaFree(w.R);
+    cudaGetLastError();
+    delete c;
+    return LLG_OK;
+}
+
+const char *llg_last_error(const llg_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+llg_status llg_set_stream(llg_ctx *c, void *stream) {
+    LLG_GUARD(c);
+    c->stream = static_cast<cudaStream_t>(stream);
+    return LLG_OK;
+}
+
+long long llg_launch_count(const llg_ctx *c) { return c ? c->launches : 0; }
+long long llg_nodes(const llg_ctx *c) { return c ? c->geo.N : 0; }
+
+llg_status llg_saddle_apply(llg_ctx *c, const llg_params *p, const double *m, const double *x, double *y, int transpose) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st != LLG_OK) return st;
+    if (!m || !x || !y) return set_error(c, LLG_ERR_INVALID_ARG, "null array");
+    if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
+    return op_matvec64(c, p, p->theta, m, x, nullptr, y, transpose);
+}
+
+llg_status llg_ffthss_apply(llg_ctx *c, const llg_params *p, const double *m, const double *pin, double *z, int transpose) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st != LLG_OK) return st;
+    if (!m || !pin || !z) return set_error(c, LLG_ERR_INVALID_ARG, "null array");
+    if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
+    return op_apply64(c, p, p->theta, m, pin, nullptr, z, transpose);
+}
+
+llg_status llg_ffthss_apply_f32(llg_ctx *c, const llg_params *p, const float *m, const float *pin, float *z, int transpose) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st != LLG_OK) return st;
+    if (!m || !pin || !z) return set_error(c, LLG_ERR_INVALID_ARG, "null array");
+    if ((st = ensure_spec(c, false, true)) != LLG_OK) return st;
+    auto io = make_io<float, float, float>(m, pin, z, nullptr, p->lambda);
+    Symbol sym = sym_shifted_inverse(c, p, p->theta);
+    if (!transpose) return spectral_chain<float, float, float>(c, IN_V, OUT_APPLY, io, sym);
+    return spectral_chain<float, float, float>(c, IN_NODAL_T, OUT_PLAIN, io, sym);
+}
+
+llg_status llg_precond_saddle_apply(llg_ctx *c, const llg_params *p, const double *m, const double *x, double *z) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st != LLG_OK) return st;
+    if (!m || !x || !z) return set_error(c, LLG_ERR_INVALID_ARG, "null array");
+    if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
+    return op_fused64(c, p, p->theta, m, x, nullptr, z);
+}
+
+llg_status llg_gmres_solve(llg_ctx *c, const llg_params *p, const llg_opts *o, const double *m, const double *b,
+                           double *x, llg_info *info) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st == LLG_OK) st = check_opts(c, o);
+    if (st != LLG_OK) return st;
+    if (!m || !b || !x) return set_error(c, LLG_ERR_INVALID_ARG, "null array");
+    llg_info inf = llg_info();
+    st = solve(c, p, p->theta, o, m, b, x, &inf);
+    inf.status = st;
+    if (info) *info = inf;
+    return st;
+}
+
+llg_status llg_energy(llg_ctx *c, const llg_params *p, const double *m, double *out) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st != LLG_OK) return st;
+    if (!m || !out) return set_error(c, LLG_ERR_INVALID_ARG, "null pointer");
+    if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
+    if ((st = ensure_aux(c)) != LLG_OK) return st;
+    if ((st = energy_async(c, p, m, c->aux, c->dsc)) != LLG_OK) return st;
+    if ((st = sync_scalars(c, 1)) != LLG_OK) return st;
+    *out = c->hsc[0] / (double)c->geo.N;
+    return LLG_OK;
+}
+
+llg_status llg_step_euler(llg_ctx *c, const llg_params *p, const llg_opts *o, const double *m_n, double *m_next,
+                          double *x_out, llg_info *info) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st == LLG_OK) st = check_opts(c, o);
+    if (st != LLG_OK) return st;
+    if (!m_n || !m_next || !x_out) return set_error(c, LLG_ERR_INVALID_ARG, "null array");
+    if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
+    if ((st = ensure_aux(c)) != LLG_OK) return st;
+    const long long N = c->geo.N;
+    double *b = c->aux;            // 4N
+    double *tmp = c->aux + 4 * N;  // 4N
+    llg_info inf = llg_info();
+    if (o->diagnostics) {
+        if ((st = energy_async(c, p, m_n, tmp, c->dsc + 8)) != LLG_OK) return st;
+    }
+    if ((st = rhs_velocity(c, p, m_n, b)) != LLG_OK) return st;
+    cudaMemsetAsync(x_out, 0, sizeof(double) * 4 * N, c->stream);
+    st = solve(c, p, 1.0, o, m_n, b, x_out, &inf);
+    if (st != LLG_OK && st != LLG_ERR_NOT_CONVERGED) { inf.status = st; if (info) *info = inf; return st; }
+    llg_status solve_st = st;
+    const int nb = reduction_blocks(c);
+    k_euler_update<<<nb, RB_THREADS, 0, c->stream>>>(m_n, x_out, p->k, m_next, N, c->red);
+    k_max_partials<<<1, 32, 0, c->stream>>>(c->red, nb, c->dsc + 9);
+    c->launches += 2;
+    if ((st = cuda_check(c, cudaGetLastError(), "euler update")) != LLG_OK) return st;
+    if (o->diagnostics) {
+        if ((st = energy_async(c, p, m_next, tmp, c->dsc + 10)) != LLG_OK) return st;
+    }
+    if ((st = sync_scalars(c, 11)) != LLG_OK) return st;
+    inf.max_len_drift = c->hsc[9];
+    if (o->diagnostics) {
+        inf.energy_before = c->hsc[8] / (double)N;
+        inf.energy_after = c->hsc[10] / (double)N;
+    }
+    inf.picard_iters = 1;
+    inf.status = solve_st;
+    if (info) *info = inf;
+    return solve_st;
+}
+
+llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o, const double *m_n, const double *v_prev,
+                             double *m_next, double *x_out, llg_info *info) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st == LLG_OK) st = check_opts(c, o);
+    if (st != LLG_OK) return st;
+    if (!m_n || !m_next || !x_out) return set_error(c, LLG_ERR_INVALID_ARG, "null array");
+    if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
+    if ((st = ensure_aux(c)) != LLG_OK) return st;
+    const long long N = c->geo.N;
+    double *b = c->aux;                // 4N
+    double *vold = c->aux + 4 * N;     // 3N
+    double *mhat = c->aux + 7 * N;     // 3N
+    double *tmp = c->aux + 10 * N;     // 4N
+    const int nb = reduction_blocks(c), gb = grid_blocks(c);
+    llg_info inf = llg_info();
+    if (o->diagnostics) {
+        if ((st = energy_async(c, p, m_n, tmp, c->dsc + 8)) != LLG_OK) return st;
+    }
+    if ((st = rhs_velocity(c, p, m_n, b)) != LLG_OK) return st;
+    k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, v_prev, 0.5 * p->k, mhat, 3 * N);
+    // warm start (v_prev | 0), or zero
+    if (v_prev) cudaMemcpyAsync(x_out, v_prev, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
+    else cudaMemsetAsync(x_out, 0, sizeof(double) * 3 * N, c->stream);
+    cudaMemsetAsync(x_out + 3 * N, 0, sizeof(double) * N, c->stream);
+    c->launches++;
+    llg_status lin_st = LLG_OK;
+    bool conv = false;
+    for (int it = 0; it < o->picard_max; ++it) {
+        llg_info si = llg_info();
+        st = solve(c, p, 0.5, o, mhat, b, x_out, &si);
+        inf.iters += si.iters;
+        inf.restarts += si.restarts;
+        inf.applies += si.applies;
+        inf.rel_res_true = std::max(inf.rel_res_true, si.rel_res_true);
+        inf.picard_iters = it + 1;
+        if (st == LLG_ERR_NOT_CONVERGED) lin_st = st;
+        else if (st != LLG_OK) { inf.status = st; if (info) *info = inf; return st; }
+        if (it >= 1) {
+            k_picard_norms<<<nb, RB_THREADS, 0, c->stream>>>(x_out, vold, 3 * N, c->red);
+            k_sum_partials_n<<<1, 32, 0, c->stream>>>(c->red, nb, 2, c->dsc);
+            c->launches += 2;
+            if ((st = sync_scalars(c, 2)) != LLG_OK) return st;
+            if (std::sqrt(c->hsc[0]) <= o->picard_tol * std::sqrt(c->hsc[1])) { conv = true; break; }
+        }
+        cudaMemcpyAsync(vold, x_out, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
+        k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, 3 * N);
+        c->launches++;
+    }
+    k_mid_final<<<nb, RB_THREADS, 0, c->stream>>>(m_n, x_out, p->k, m_next, N, c->red);
+    k_max_partials<<<1, 32, 0, c->stream>>>(c->red, nb, c->dsc + 9);
+    c->launches += 2;
+    if ((st = cuda_check(c, cudaGetLastError(), "midpoint update")) != LLG_OK) return st;
+    if (o->diagnostics) {
+        if ((st = energy_async(c, p, m_next, tmp, c->dsc + 10)) != LLG_OK) return st;
+        if ((st = dot_async(c, x_out, x_out, 3 * N, c->dsc + 11)) != LLG_OK) return st;
+    }
+    if ((st = sync_scalars(c, 12)) != LLG_OK) return st;
+    inf.max_len_drift = c->hsc[9];
+    if (o->diagnostics) {
+        inf.energy_before = c->hsc[8] / (double)N;
+        inf.energy_after = c->hsc[10] / (double)N;
+        const double v2 = c->hsc[11] / (double)N;
+        inf.dissipation_residual = inf.energy_after - inf.energy_before + p->alpha * p->k / (1.0 + p->alpha * p->alpha) * v2;
+    }
+    llg_status res = lin_st != LLG_OK ? lin_st : (conv ? LLG_OK : LLG_ERR_NOT_CONVERGED);
+    if (res == LLG_ERR_NOT_CONVERGED && c->err.empty()) set_error(c, res, "Picard iteration reached picard_max");
+    inf.status = res;
+    if (info) *info = inf;
+    return res;
+}
+
+llg_status llg_adjoint_step(llg_ctx *c, const llg_params *p, const llg_opts *o, const double *m_n, const double *x,
+                            const double *mbar_next, double *mbar_n, double *dalpha, double dh[3], llg_info *info) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st == LLG_OK) st = check_opts(c, o);
+    if (st != LLG_OK) return st;
+    if (!m_n || !x || !mbar_next || !mbar_n || !dalpha || !dh) return set_error(c, LLG_ERR_INVALID_ARG, "null pointer");
+    if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
+    if ((st = ensure_aux(c)) != LLG_OK) return st;
+    const long long N = c->geo.N;
+    double *y = c->aux;               // 4N
+    double *mhat = c->aux + 4 * N;    // 3N
+    double *rhs = c->aux + 7 * N;     // 4N
+    double *lapy = c->aux + 11 * N;   // 4N (3 used)
+    double *u = c->aux + 15 * N;      // 3N
+    double *lapu = c->aux + 18 * N;   // 4N (3 used)
+    const int nb = reduction_blocks(c), gb = grid_blocks(c);
+    const double hk = 0.5 * p->k;
+    k_adj_prep<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x, mbar_next, p->k, p->alpha * p->c_ex, mhat, rhs, u, N);
+    cudaMemsetAsync(y, 0, sizeof(double) * 4 * N, c->stream);
+    c->launches++;
+    if ((st = check_nodes(c, mhat)) != LLG_OK) return st;
+    // J^T and the transposed preconditioner M(mhat)^{-T}
+    Symbol fwd = sym_forward(c, p, 0.5);
+    Symbol inv = sym_shifted_inverse(c, p, 0.5);
+    auto jt = [=](const double *xx, const double *s, double *yy) {
+        auto io = make_io<double, double, double>(mhat, xx, yy, s, p->lambda);
+        io.mn = m_n; io.vf = x; io.half_k = hk;
+        return spectral_chain<double, double, double>(c, IN_V, OUT_JT, io, fwd);
+    };
+    auto pt = [=](const double *xx, const double *s, double *yy) {
+        auto io = make_io<double, double, double>(mhat, xx, yy, s, p->lambda);
+        return spectral_chain<double, double, double>(c, IN_NODAL_T, OUT_PLAIN, io, inv);
+    };
+    SolveOps ops;
+    ops.matvec = [=](const double *xx, double *yy) { return jt(xx, nullptr, yy); };
+    ops.prec = pt;
+    ops.pop = [=](const double *xx, const double *s, double *yy) {
+        llg_status s2 = jt(xx, s, c->ws.R);
+        if (s2 != LLG_OK) return s2;
+        return pt(c->ws.R, nullptr, yy);
+    };
+    llg_opts o64 = *o;
+    o64.precision = LLG_PREC_FP64;
+    llg_info inf = llg_info();
+    llg_status solve_st = gmres_run(c, ops, false, &o64, rhs, y, &inf);
+    if (solve_st != LLG_OK && solve_st != LLG_ERR_NOT_CONVERGED) { inf.status = solve_st; if (info) *info = inf; return solve_st; }
+    inf.applies *= 2;
+    // Chat (-Lap) y_v and (-Lap) u
+    {
+        auto io = make_io<double, double, double>(mhat, y, lapy, nullptr, p->lambda);
+        Symbol s{0.0, chat(p), 1.0 / (double)N, 0, p->exchange};
+        if ((st = spectral_chain<double, double, double>(c, IN_V, OUT_PLAIN, io, s)) != LLG_OK) return st;
+        auto io2 = make_io<double, double, double>(mhat, u, lapu, nullptr, p->lambda);
+        Symbol s2{0.0, 1.0, 1.0 / (double)N, 0, p->exchange};
+        if ((st = spectral_chain<double, double, double>(c, IN_V, OUT_PLAIN, io2, s2)) != LLG_OK) return st;
+    }
+    k_adj_final<<<nb, RB_THREADS, 0, c->stream>>>(mbar_next, y, lapy, x, lapu, p->alpha, p->h_ext[0], p->h_ext[1],
+                                                  p->h_ext[2], mbar_n, N, c->red);
+    k_sum_partials_n<<<1, 32, 0, c->stream>>>(c->red, nb, 4, c->dsc);
+    c->launches += 2;
+    if ((st = cuda_check(c, cudaGetLastError(), "adjoint")) != LLG_OK) return st;
+    if ((st = sync_scalars(c, 4)) != LLG_OK) return st;
+    const double s = 1.0 + p->alpha * p->alpha;
+    *dalpha += c->hsc[0];
+    for (int q = 0; q < 3; ++q) dh[q] += s * c->hsc[1 + q];
+    inf.status = solve_st;
+    if (info) *info = inf;
+    return solve_st;
+}
+
+}  // extern "C"

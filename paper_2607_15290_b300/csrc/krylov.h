@@ -1,0 +1,44 @@
+// krylov.h -- device-side Arnoldi state and the GMRES driver interface.
+#pragma once
+#include <functional>
+#include "llg_internal.h"
+
+namespace llg {
+
+// Arnoldi state of one GMRES cycle, resident in device memory.  The small
+// header (flags, counters) comes first so the host can poll it cheaply.
+struct GmresDev {
+    static constexpr int MAXM = 64;
+    static constexpr int LD = MAXM + 1;
+    int done;        // cycle finished (converged estimate, breakdown or happy breakdown)
+    int jd;          // Arnoldi steps completed in this cycle
+    int breakdown;   // non-finite value met
+    int m;           // restart length of the cycle
+    double target;   // stop when |g_{j+1}| <= target
+    double pad[3];
+    double H[LD * MAXM];   // Hessenberg, column-major, rotated in place
+    double cs[MAXM], sn[MAXM];
+    double g[LD];          // rotated right-hand side beta e1
+    double y[MAXM], coef[MAXM];
+    double scale[LD];      // 1 / ||V_i|| of the stored (unnormalised) basis vectors
+    double h1[MAXM], h2[MAXM];
+};
+static constexpr size_t GMRES_HEADER_BYTES = 32;
+
+struct SolveOps {
+    // y = A x in FP64 (true residual)
+    std::function<llg_status(const double *x, double *y)> matvec;
+    // y = M^{-1} (s x) in FP64, s = *scale (NULL: 1)
+    std::function<llg_status(const double *x, const double *scale, double *y)> prec;
+    // y = M^{-1} A (s x) in FP64 (left-preconditioned operator)
+    std::function<llg_status(const double *x, const double *scale, double *y)> pop;
+    // flexible GMRES: z = P(s x) stored FP32, then w = A z stored FP64
+    std::function<llg_status(const double *x, const double *scale, float *z)> fprec;
+    std::function<llg_status(const float *z, double *w)> fmatvec;
+};
+
+llg_status ensure_workspace(llg_ctx *c, int restart, bool flexible);
+llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_opts *o, const double *b, double *x,
+                     llg_info *info);
+
+}  // namespace llg

@@ -1,0 +1,118 @@
+// llg_internal.h -- context, workspace and launcher declarations shared by the
+// CUDA translation units of the library (not part of the public C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <functional>
+#include "../../include/llg.h"
+
+namespace llg {
+
+// Spectral buffer layout.  For every grid row (fixed y, z) the x-axis transform
+// stores S complex slots: [0, n0) the full spectrum of the packed pair
+// (c1 + i c2), [n0, n0 + n0/2] the half spectrum of the real component c3,
+// and zero padding up to S (a multiple of 16 so that column tiles are uniform).
+struct SpecGeom {
+    int n[3];
+    int logn[3];
+    int dim;
+    long long N;      // nodes
+    long long rows;   // n1 * n2
+    int S;            // complex slots per row
+};
+
+// Prologue (what is transformed) and epilogue (what is written) of a spectral
+// chain: forward x-pass, axis passes with the symbol, inverse x-pass.
+enum InMode {
+    IN_V = 0,       // c = s * (v1, v2, v3)
+    IN_FUSED = 1,   // c = s * (m x v + m r - lambda v)         [left-preconditioned operator]
+    IN_M = 2,       // c = (m1, m2, m3)                          [Laplacian of the nodal field]
+    IN_NODAL_T = 3, // (z, zr) = (S~ + lambda)^{-T} s x; c = z; y_r = zr / lambda   [M^{-T}]
+};
+enum OutMode {
+    OUT_APPLY = 0,   // y = (S~ + lambda)^{-1} (w, s r / lambda)
+    OUT_FUSED = 1,   // y = (S~ + lambda)^{-1} (s v + w, -s (m.v) / lambda)
+    OUT_MATVEC = 2,  // y_v = w + s (m x v + m r), y_r = -s m.v     (transpose: signs of the skew part flip)
+    OUT_FIELD = 3,   // y_v = w + fld, y_r = 0
+    OUT_PLAIN = 4,   // y_v = w (y_r untouched)
+    OUT_JT = 5,      // adjoint Jacobian transpose of a midpoint step (see api.cu)
+};
+
+// Pointwise Fourier multiplier: scale * (a + b sigma) or scale / (a + b sigma)
+struct Symbol {
+    double a, b, scale;
+    int invert;
+    int exchange;   // which sigma table
+};
+
+template <typename TIn, typename TOut, typename T>
+struct NodalIO {
+    const T *m;            // nodal field used by the prologue/epilogue (3 planes, precision T)
+    const TIn *x;          // input planes (4 planes; 3 for IN_M)
+    TOut *y;               // output planes (4)
+    const double *scale;   // optional device scalar s (NULL = 1)
+    T lam;
+    T fld[3];
+    int transpose;         // OUT_MATVEC: use A^T
+    // OUT_JT only
+    const T *mn;           // m^n (3 planes)
+    const T *vf;           // forward velocity v (3 planes) and r (1 plane, at vf + 3N)
+    T half_k;              // k / 2
+};
+
+struct Workspace {
+    int restart = 0;
+    long long n = 0;          // 4 N
+    double *V = nullptr;      // (restart + 1) * n
+    float *Z = nullptr;       // restart * n (flexible GMRES)
+    double *W = nullptr;      // n
+    double *T = nullptr;      // n
+    double *R = nullptr;      // n
+};
+
+struct GmresDev;   // device-side Arnoldi state (krylov.cu)
+
+}  // namespace llg
+
+struct llg_ctx {
+    llg_grid grid;
+    cudaStream_t stream = nullptr;
+    llg::SpecGeom geo;
+    // per-axis twiddle tables exp(-2 pi i j / n_axis), FP64 and FP32
+    double2 *tw64[3] = {nullptr, nullptr, nullptr};
+    float2 *tw32[3] = {nullptr, nullptr, nullptr};
+    // per-axis symbol tables sigma_axis(index) for [spectral, fd2]
+    double *sig64[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    float *sig32[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    double2 *spec64 = nullptr;   // spectral scratch, rows * S
+    float2 *spec32 = nullptr;
+    double *red = nullptr;       // reduction partials
+    double *dsc = nullptr;       // small device scalars (norms, flags)
+    double *hsc = nullptr;       // pinned host mirror of dsc
+    llg::GmresDev *gdev = nullptr;
+    void *ghost = nullptr;       // pinned host mirror of gdev
+    llg::Workspace ws;
+    float *m32 = nullptr;        // FP32 copy of the nodal field (mixed precision)
+    double *aux = nullptr;       // 12 N doubles of stepper scratch
+    int sm_count = 148;
+    int sync_every = 4;
+    long long launches = 0;      // kernels launched through this context
+    std::string err;
+};
+
+namespace llg {
+
+llg_status set_error(llg_ctx *c, llg_status s, const std::string &msg);
+llg_status cuda_check(llg_ctx *c, cudaError_t e, const char *what);
+
+// spectral.cu
+template <typename T, typename TIn, typename TOut>
+llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<TIn, TOut, T> &io,
+                          const Symbol &sym);
+
+// reductions.cu / krylov.cu
+int reduction_blocks(llg_ctx *c);
+llg_status dot_async(llg_ctx *c, const double *a, const double *b, long long n, double *dst_dev);
+
+}  // namespace llg

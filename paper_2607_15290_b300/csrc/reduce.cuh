@@ -1,0 +1,57 @@
+// reduce.cuh -- deterministic block reductions: every block writes its partial
+// sums to partials[block * 64 + i]; a single block then sums them in a fixed
+// order, so results do not depend on scheduling.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace llg {
+
+static constexpr int RB_THREADS = 256;
+static constexpr int RB_STRIDE = 64;
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, double *out) {
+    __shared__ double red[RB_THREADS / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        if (i < nv) {
+            double v = acc[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][i] = v;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < RB_THREADS / 32; ++w) s += red[w][i];
+        out[i] = s;
+    }
+}
+
+__device__ __forceinline__ void block_max_store(double v, double *out) {
+    __shared__ double red[RB_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = red[0];
+        for (int w = 1; w < RB_THREADS / 32; ++w) s = fmax(s, red[w]);
+        *out = s;
+    }
+}
+
+// chunk [lo, hi) of n elements owned by this block (contiguous)
+__device__ __forceinline__ void block_chunk(long long n, long long &lo, long long &hi) {
+    long long per = (n + gridDim.x - 1) / gridDim.x;
+    per = (per + 1) & ~1LL;
+    lo = per * blockIdx.x;
+    hi = lo + per;
+    if (lo > n) lo = n;
+    if (hi > n) hi = n;
+}
+
+}  // namespace llg
