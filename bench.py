@@ -1,0 +1,391 @@
+"""Benchmark of the FFT--HSS preconditioned GMRES hot path on one B300.
+
+Workload (default): the 3D periodic 128^3 grid (2,097,152 nodes, 8.4M unknowns),
+smooth synthetic field m = normalise((cos 2pi z sin 2pi x, sin 2pi z sin 2pi y,
+cos 2pi x) + 1e-3 seeded noise), alpha = 0.1, h = (0, 0, 0.5), lambda = 0.5,
+dt = 4x the explicit exchange limit, Crank--Nicolson-type midpoint steps with
+Picard iteration, each linear solve by flexible GMRES(30) with the FFT--HSS
+application and its inner matvec in FP32 and the Arnoldi process, least
+squares, true residual and nodal update in FP64, rtol 1e-10.
+
+One step = one midpoint time step (right-hand side, every Picard solve with all
+its FFT--HSS applications and Arnoldi steps, the nodal update and the drift).
+value = FFT--HSS applications per second over the timed steps (all ranks).
+Also reported: the same system solved by all-FP64 FFT--HSS GMRES vs the FP32
+flexible solve (ms per solve, same rtol), the isolated FP32 apply at 128^3 and
+256^3 (applies/s and algorithmic GB/s), the dominant kernel class against its
+roofline (timed live with CUDA events on the context's stream during the timed
+steps), the oracle on the host cores, and an end-to-end figure through host
+buffers.  Inputs (fields, the Krylov basis) are far larger than the 126 MB L2.
+
+--impl reference runs the CPU oracle (the plain FP64 reference written from the
+paper) on the same workload: each step is one oracle FFT--HSS application of the
+128^3 field (radix-2 FFT mode), a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FFT-HSS applies/s + HBM GB/s; GMRES solve ms at 128^3, FP32-prec FGMRES vs FP64"
+UNIT = "applies/s"
+WORKLOAD = "llg-midpoint-3d-128: 128^3 periodic, smooth field, alpha 0.1, dt 4x explicit limit, FP32-flex FGMRES(30)"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6400.0, "fallback": True}
+
+
+def workload_params(n=128):
+    import numpy as np
+    alpha = 0.1
+    sig_max = 3 * (math.pi * n) ** 2           # max |xi|^2 on the unit cube (Nyquist |k| = n/2)
+    k_ex = 2 * alpha / ((1 + alpha ** 2) * sig_max)
+    return dict(alpha=alpha, k=4 * k_ex, k_ex=k_ex, h=(0.0, 0.0, 0.5), lam=0.5, n=(n, n, n))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except Exception:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_baseline(seconds=12.0):
+    """The oracle as it stands, timed on the host cores on a bounded sample: repeated FP64
+    FFT--HSS applications of the 128^3 field in the oracle's radix-2 FFT mode."""
+    import numpy as np
+    import oracle as O
+    from paper_2607_15290_b300 import inputs as I
+    w = workload_params()
+    g = O.Grid(w["n"])
+    prm = O.Params(alpha=w["alpha"], k=w["k"], theta=0.5, lam=w["lam"], h=w["h"])
+    m = I.smooth3d(w["n"])
+    p = I.random_saddle_vector(w["n"], seed=5)
+    O.set_transform(O.FFT)
+    t0 = time.perf_counter()
+    count = 0
+    while True:
+        O.ffthss_apply(g, prm, m, p)
+        count += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    O.set_transform(O.DFT)
+    return {"value": count / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{count} oracle FP64 FFT-HSS applications of the 128^3 field (radix-2 FFT mode, "
+                      f"single thread) in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    from paper_2607_15290_b300 import inputs as I
+    w = workload_params()
+    g = O.Grid(w["n"])
+    prm = O.Params(alpha=w["alpha"], k=w["k"], theta=0.5, lam=w["lam"], h=w["h"])
+    m = I.smooth3d(w["n"])
+    p = I.random_saddle_vector(w["n"], seed=5)
+    O.set_transform(O.FFT)
+    for _ in range(args.warmup):
+        O.ffthss_apply(g, prm, m, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.ffthss_apply(g, prm, m, p)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "reference_step": "one oracle FFT-HSS apply"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} oracle FP64 FFT-HSS applications of the 128^3 field "
+                                      "(radix-2 FFT mode, single thread)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--roofline-class", default="arnoldi", choices=["xfwd", "axis", "xinv", "arnoldi"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, apply sweep and e2e legs")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_2607_15290_b300 as L
+    from paper_2607_15290_b300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = workload_params()
+    n = w["n"]
+    N = n[0] * n[1] * n[2]
+    ctx = L.Context(n)
+    prm = L.Params(alpha=w["alpha"], k=w["k"], theta=0.5, lam=w["lam"], h_ext=w["h"])
+    opts = L.Opts(restart=30, rtol=1e-10, precision=L.PREC_FP32_FLEX, picard_tol=1e-10, picard_max=50)
+    m0 = torch.tensor(I.smooth3d(n), device="cuda")
+    x = ctx.empty(4)
+    mA, mB = m0.clone(), ctx.empty(3)
+    stream = ctx.stream
+
+    def step(m_in, m_out, vprev):
+        _, _, info = L.llg_step_midpoint(ctx, prm, opts, m_in, vprev, m_out, x)
+        return info
+
+    vprev = None
+    for _ in range(args.warmup):
+        step(mA, mB, vprev)
+        vprev = x[:3].clone()
+        mA, mB = mB, mA
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launches()
+    barrier()
+    clocks.start()
+    ctx.profile_begin(args.roofline_class)
+    ev0.record(stream)
+    applies = solves = iters = 0
+    drift = 0.0
+    for _ in range(args.steps):
+        info = step(mA, mB, vprev)
+        applies += info["applies"]
+        solves += info["picard_iters"]
+        iters += info["iters"]
+        drift = max(drift, info["max_len_drift"])
+        vprev = x[:3].clone()
+        mA, mB = mB, mA
+    ev1.record(stream)
+    barrier()
+    prof = ctx.profile_end()
+    clk = clocks.stop()
+    gpu_launches = ctx.launches() - l0
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        a = torch.tensor([applies], device="cuda", dtype=torch.float64)
+        dist.all_reduce(a)
+        applies_total = float(a.item())
+    else:
+        applies_total = applies
+    value = applies_total / (ms / 1e3)
+
+    extras = {}
+    pk = peaks()
+    if not args.no_extras and rank == 0:
+        extras = extras_leg(L, I, ctx, prm, w, m0, args)
+    fp64_peak = ctx.probe_fma_rate(True)
+    fp32_peak = ctx.probe_fma_rate(False)
+
+    # roofline of the profiled (dominant) kernel class
+    avg_ms = prof["ms"] / max(prof["launches"], 1)
+    if args.roofline_class == "arnoldi":
+        achieved = prof["flops"] / (prof["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "kernel": "arnoldi_pass (FP64 CGS2 multi-dot/update)", "launches": prof["launches"],
+                "avg_launch_ms": avg_ms, "hbm_gbs_at_algorithmic_bytes": prof["bytes"] / (prof["ms"] / 1e3) / 1e9,
+                "peak_source": "FP64 FMA rate measured live on this device (llg_probe_fma_rate); nominal 1.25"}
+    else:
+        achieved = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": args.roofline_class,
+                "launches": prof["launches"], "avg_launch_ms": avg_ms,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" + (" (fallback)" if pk.get("fallback") else "")}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (FP32 FFT-HSS + inner matvec, FP64 Arnoldi)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(n), "nodes": N, "unknowns": 4 * N, "alpha": w["alpha"],
+                   "dt": w["k"], "dt_over_explicit_limit": 4.0, "lambda": w["lam"], "h_ext": list(w["h"]),
+                   "restart": 30, "rtol": 1e-10, "picard_tol": 1e-10,
+                   "l2": "inputs larger than L2 (fields 50-67 MB each, Krylov basis ~2 GB)",
+                   "parallelism": f"replicas x{world} (independent problems, no collective)"},
+        "solves_per_s": solves * world / (ms / 1e3), "steps_per_s": args.steps * world / (ms / 1e3),
+        "gmres_iters_per_solve": iters / max(solves, 1), "max_len_drift": drift,
+        "roofline": roof, "gpu_launches": gpu_launches, "clocks": clk,
+        "fp64_fma_tflops_measured": fp64_peak, "fp32_fma_tflops_measured": fp32_peak,
+    }
+    out.update(extras)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = oracle_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def extras_leg(L, I, ctx, prm, w, m0, args):
+    """FP32-flexible vs all-FP64 solve of one identical system, the isolated apply sweep and
+    the end-to-end (host buffer) figure.  Runs after the timed region."""
+    import torch
+    ex = {}
+    n = w["n"]
+    stream = ctx.stream
+
+    def events_ms(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # the first Picard system of a midpoint step from m0: A(m0; theta=1/2) x = b
+    b = ctx.empty(4)
+    x0 = ctx.empty(4)
+    L.llg_step_midpoint(ctx, prm, L.Opts(picard_max=1, rtol=1e-3), m0, None, ctx.empty(3), x0,
+                        raise_on_error=False)
+    # right-hand side of that system: b = A x0 (a consistent system with a known solution)
+    L.llg_saddle_apply(ctx, prm, m0, x0, out=b)
+    res = {}
+    for name, prec in (("fp32flex", L.PREC_FP32_FLEX), ("fp64", L.PREC_FP64)):
+        o = L.Opts(restart=30, rtol=1e-10, precision=prec)
+        times, its, rr, err = [], 0, 0.0, 0.0
+        for rep in range(4):
+            x = torch.zeros_like(b)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            x, info = L.llg_gmres_solve(ctx, prm, o, m0, b, x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                times.append(e0.elapsed_time(e1))
+            its, rr = info["iters"], info["rel_res_true"]
+            err = float((x - x0).abs().max() / x0.abs().max())
+        times.sort()
+        res[name] = {"ms": times[len(times) // 2], "iters": its, "rel_res_true": rr, "rel_err_vs_known_x": err}
+    ex["solve_128"] = res
+    ex["solve_ms_fp32flex"] = res["fp32flex"]["ms"]
+    ex["solve_ms_fp64"] = res["fp64"]["ms"]
+    ex["speedup_fp32flex_vs_fp64"] = res["fp64"]["ms"] / res["fp32flex"]["ms"]
+
+    # isolated FP32 FFT-HSS apply: 128^3 (this context) and 256^3
+    def apply_rate(c2, nn):
+        N = nn[0] * nn[1] * nn[2]
+        mm = torch.tensor(I.smooth3d(nn), device="cuda").float()
+        p = torch.randn((4,) + tuple(reversed(nn)), device="cuda", dtype=torch.float32)
+        z = torch.empty_like(p)
+        t = events_ms(lambda: L.llg_ffthss_apply_f32(c2, prm, mm, p, out=z), 20)
+        algo = (11 + 24) * 4 * N        # inputs v, r, m + output z, and the 5-pass plan's 4 spectral passes
+        floor = 11 * 4 * N
+        return {"ms": t, "applies_per_s": 1e3 / t, "gbs_algorithmic_5pass": algo / t / 1e6,
+                "gbs_io_floor": floor / t / 1e6}
+    ex["apply_fp32_128"] = apply_rate(ctx, n)
+    c256 = L.Context((256, 256, 256))
+    ex["apply_fp32_256"] = apply_rate(c256, (256, 256, 256))
+    c256.close()
+    torch.cuda.empty_cache()
+
+    # end to end through host buffers: H2D of m^n from pinned memory, the step, D2H of m^{n+1}
+    opts = L.Opts(restart=30, rtol=1e-10, precision=L.PREC_FP32_FLEX, picard_tol=1e-10)
+    mh = m0.cpu().pin_memory()
+    outh = torch.empty_like(mh).pin_memory()
+    md, mo, xx = ctx.empty(3), ctx.empty(3), ctx.empty(4)
+    steps = max(2, min(args.steps, 5))
+    applies = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        md.copy_(mh, non_blocking=True)
+        _, _, info = L.llg_step_midpoint(ctx, prm, opts, md, None, mo, xx)
+        outh.copy_(mo, non_blocking=True)
+        applies += info["applies"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1)
+    ex["e2e"] = {"value": applies / (t / 1e3), "unit": UNIT, "h2d_bytes_per_step": mh.numel() * 8,
+                 "d2h_bytes_per_step": outh.numel() * 8, "steps": steps,
+                 "note": "each step copies m^n host->device, runs the midpoint step cold (no warm start) "
+                         "and copies m^{n+1} back"}
+    return ex
+
+
+if __name__ == "__main__":
+    main()

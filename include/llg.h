@@ -162,6 +162,29 @@ llg_status llg_adjoint_step(llg_ctx *ctx, const llg_params *prm, const llg_opts 
    *out is a HOST pointer; synchronises the stream. */
 llg_status llg_energy(llg_ctx *ctx, const llg_params *prm, const double *m, double *out);
 
+/* ---------------------------------------------------------------- measurement support
+   (infrastructure for the benchmark; no counterpart in the paper) */
+
+/* kernel classes that can be timed live */
+enum {
+    LLG_KCLASS_NONE = 0,
+    LLG_KCLASS_XFWD = 1,     /* forward x-axis pass with the nodal prologue */
+    LLG_KCLASS_AXIS = 2,     /* y/z axis passes (with the Fourier multiplier on the last axis) */
+    LLG_KCLASS_XINV = 3,     /* inverse x-axis pass with the nodal epilogue */
+    LLG_KCLASS_ARNOLDI = 4   /* Gram--Schmidt passes over the Krylov basis */
+};
+/* Start timing every launch of one kernel class on this context: a CUDA event pair is
+   recorded on the context's stream around each launch, together with the launch's
+   algorithmic bytes and flops (inputs read + outputs written once; 5 n log2 n flops per
+   complex length-n transform; 2 per multiply-add).  Launches of an Arnoldi step that the
+   device-side stopping flag turned into no-ops are discarded. */
+llg_status llg_profile_begin(llg_ctx *ctx, int kernel_class);
+/* Stop timing, synchronise the stream and return the totals (HOST pointers, any may be NULL). */
+llg_status llg_profile_end(llg_ctx *ctx, double *total_ms, long long *launches, double *bytes, double *flops);
+/* Measure the device's multiply-add rate with a register-resident FMA loop on the context's
+   stream (fp64 != 0: double, else float); *tflops receives 2 * FMAs / s / 1e12 (HOST). */
+llg_status llg_probe_fma_rate(llg_ctx *ctx, int fp64, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,22 @@ class Context:
     def launches(self):
         return int(self.lib.llg_launch_count(self.h))
 
+    def profile_begin(self, kernel_class):
+        """Time every launch of one kernel class ('xfwd', 'axis', 'xinv', 'arnoldi') live."""
+        self._check(self.lib.llg_profile_begin(self.h, _abi.KCLASS[kernel_class]))
+
+    def profile_end(self):
+        """Returns dict(ms, launches, bytes, flops) summed over the profiled launches."""
+        ms, n, by, fl = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+        self._check(self.lib.llg_profile_end(self.h, C.byref(ms), C.byref(n), C.byref(by), C.byref(fl)))
+        return {"ms": ms.value, "launches": n.value, "bytes": by.value, "flops": fl.value}
+
+    def probe_fma_rate(self, fp64=True):
+        """Measured multiply-add rate of this device in TFLOP/s (FP64 or FP32)."""
+        out = C.c_double()
+        self._check(self.lib.llg_probe_fma_rate(self.h, int(fp64), C.byref(out)))
+        return out.value
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.llg_destroy(self.h)

@@ -31,7 +31,9 @@ EXPORTS = [
     "llg_create", "llg_destroy", "llg_last_error", "llg_set_stream", "llg_launch_count", "llg_nodes",
     "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_precond_saddle_apply",
     "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy",
+    "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate",
 ]
+KCLASS = {"xfwd": 1, "axis": 2, "xinv": 3, "arnoldi": 4}
 
 
 class Grid(C.Structure):
@@ -90,6 +92,9 @@ def lib():
     L.llg_step_midpoint.argtypes = [ctx, P(Params), P(Opts), vp, vp, vp, vp, P(Info)]
     L.llg_adjoint_step.argtypes = [ctx, P(Params), P(Opts), vp, vp, vp, vp, d, d, P(Info)]
     L.llg_energy.argtypes = [ctx, P(Params), vp, d]
+    L.llg_profile_begin.argtypes = [ctx, C.c_int]
+    L.llg_profile_end.argtypes = [ctx, d, P(C.c_longlong), d, d]
+    L.llg_probe_fma_rate.argtypes = [ctx, C.c_int, d]
     for name in EXPORTS:
         if name not in ("llg_last_error", "llg_launch_count", "llg_nodes"):
             getattr(L, name).restype = C.c_int

@@ -27,7 +27,55 @@ llg_status cuda_check(llg_ctx *c, cudaError_t e, const char *what) {
                      std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+void prof_begin(llg_ctx *c, int cls, double bytes, double flops, int tag) {
+    c->prof_open = -1;
+    if (c->prof_class == 0 || cls != c->prof_class) return;
+    if (c->prof_used == c->prof.size()) {
+        if (c->prof.size() >= 65536) return;
+        llg_ctx::ProfEntry e{};
+        if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        c->prof.push_back(e);
+    }
+    llg_ctx::ProfEntry &e = c->prof[c->prof_used];
+    e.bytes = bytes;
+    e.flops = flops;
+    e.tag = tag;
+    e.valid = 1;
+    cudaEventRecord(e.a, c->stream);
+    c->prof_open = (int)c->prof_used++;
+}
+
+void prof_end(llg_ctx *c) {
+    if (c->prof_open < 0) return;
+    cudaEventRecord(c->prof[c->prof_open].b, c->stream);
+    c->prof_open = -1;
+}
+
+// drop entries recorded since `first` whose tag (Arnoldi step index) is >= min_tag:
+// those launches found the cycle's stopping flag set and did no work
+void prof_discard(llg_ctx *c, size_t first, int min_tag) {
+    for (size_t i = first; i < c->prof_used; ++i)
+        if (c->prof[i].tag >= min_tag) c->prof[i].valid = 0;
+}
+
 // ------------------------------------------------------------------ small kernels
+
+template <typename T>
+__global__ void k_fma_probe(T *out, int iters) {
+    T a[8];
+    for (int i = 0; i < 8; ++i) a[i] = (T)(threadIdx.x + i) * (T)1e-3;
+    const T b = (T)0.9999999, cc = (T)1e-7;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = fma(a[i], b, cc);
+    }
+    T s = 0;
+    for (int i = 0; i < 8; ++i) s += a[i];
+    out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
 
 __global__ void k_min_norm2(const double *__restrict__ m, long long N, double *partials) {
     long long lo, hi;
@@ -437,6 +485,7 @@ llg_status llg_destroy(llg_ctx *c) {
     }
     cudaFree(c->spec64); cudaFree(c->spec32); cudaFree(c->red); cudaFree(c->dsc);
     cudaFree(c->gdev); cudaFree(c->m32); cudaFree(c->aux);
+    for (auto &e : c->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->ghost) cudaFreeHost(c->ghost);
     Workspace &w = c->ws;
@@ -447,6 +496,69 @@ llg_status llg_destroy(llg_ctx *c) {
 }
 
 const char *llg_last_error(const llg_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+llg_status llg_profile_begin(llg_ctx *c, int kernel_class) {
+    LLG_GUARD(c);
+    if (kernel_class < LLG_KCLASS_NONE || kernel_class > LLG_KCLASS_ARNOLDI)
+        return set_error(c, LLG_ERR_INVALID_ARG, "unknown kernel class");
+    c->prof_class = kernel_class;
+    c->prof_used = 0;
+    c->prof_open = -1;
+    return LLG_OK;
+}
+
+llg_status llg_profile_end(llg_ctx *c, double *total_ms, long long *launches, double *bytes, double *flops) {
+    LLG_GUARD(c);
+    llg_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "profile sync");
+    if (st != LLG_OK) return st;
+    double ms = 0.0, by = 0.0, fl = 0.0;
+    long long n = 0;
+    for (size_t i = 0; i < c->prof_used; ++i) {
+        const llg_ctx::ProfEntry &e = c->prof[i];
+        if (!e.valid) continue;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, e.a, e.b) != cudaSuccess) { cudaGetLastError(); continue; }
+        ms += t;
+        by += e.bytes;
+        fl += e.flops;
+        ++n;
+    }
+    c->prof_class = 0;
+    c->prof_used = 0;
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = n;
+    if (bytes) *bytes = by;
+    if (flops) *flops = fl;
+    return LLG_OK;
+}
+
+llg_status llg_probe_fma_rate(llg_ctx *c, int fp64, double *tflops) {
+    LLG_GUARD(c);
+    if (!tflops) return set_error(c, LLG_ERR_INVALID_ARG, "null pointer");
+    const int blocks = c->sm_count * 8, threads = 256, iters = fp64 ? 4000 : 40000;
+    void *out = nullptr;
+    cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * 8);
+    if (e != cudaSuccess) return cuda_check(c, e, "probe buffer");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {   // first launch warms up
+        cudaEventRecord(e0, c->stream);
+        if (fp64) k_fma_probe<double><<<blocks, threads, 0, c->stream>>>((double *)out, iters);
+        else k_fma_probe<float><<<blocks, threads, 0, c->stream>>>((float *)out, iters);
+        cudaEventRecord(e1, c->stream);
+    }
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    c->launches += 2;
+    if (e != cudaSuccess) return cuda_check(c, e, "probe");
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
+    return LLG_OK;
+}
 
 llg_status llg_set_stream(llg_ctx *c, void *stream) {
     LLG_GUARD(c);

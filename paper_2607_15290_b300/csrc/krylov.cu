@@ -230,8 +230,8 @@ static void launch_pass(llg_ctx *c, int mode, const double *V, long long ldv, in
         arnoldi_pass<MAXV, PASS_UPD_NRM><<<nb, RB_THREADS, 0, c->stream>>>(V, ldv, nv, gd, win, wout, n, c->red);
 }
 
-static void pass_dispatch(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const double *win, double *wout,
-                          long long n) {
+static void pass_dispatch_raw(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const double *win, double *wout,
+                              long long n) {
     if (nv <= 4) launch_pass<4>(c, mode, V, ldv, nv, win, wout, n);
     else if (nv <= 8) launch_pass<8>(c, mode, V, ldv, nv, win, wout, n);
     else if (nv <= 16) launch_pass<16>(c, mode, V, ldv, nv, win, wout, n);
@@ -239,16 +239,26 @@ static void pass_dispatch(llg_ctx *c, int mode, const double *V, long long ldv, 
     else launch_pass<64>(c, mode, V, ldv, nv, win, wout, n);
 }
 
+static void pass_dispatch(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const double *win, double *wout,
+                          long long n, int j) {
+    const double nd = (double)n;
+    const double bytes = 8.0 * nd * (mode == PASS_DOT ? nv + 1 : nv + 2);
+    const double flops = nd * (mode == PASS_DOT ? 2.0 * nv : (mode == PASS_UPD_DOT ? 4.0 * nv : 2.0 * nv + 2.0));
+    prof_begin(c, K_ARNOLDI, bytes, flops, j);
+    pass_dispatch_raw(c, mode, V, ldv, nv, win, wout, n);
+    prof_end(c);
+}
+
 // one Arnoldi step j on w = W (CGS2); writes the unnormalised V_{j+1}
 static llg_status arnoldi_step(llg_ctx *c, int j) {
     Workspace &w = c->ws;
     const long long n = w.n;
     const int nb = reduction_blocks(c), nv = j + 1;
-    pass_dispatch(c, PASS_DOT, w.V, n, nv, w.W, nullptr, n);
+    pass_dispatch(c, PASS_DOT, w.V, n, nv, w.W, nullptr, n, j);
     arnoldi_reduce<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, nv, c->gdev, 0, j);
-    pass_dispatch(c, PASS_UPD_DOT, w.V, n, nv, w.W, w.W, n);
+    pass_dispatch(c, PASS_UPD_DOT, w.V, n, nv, w.W, w.W, n, j);
     arnoldi_reduce<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, nv, c->gdev, 1, j);
-    pass_dispatch(c, PASS_UPD_NRM, w.V, n, nv, w.W, w.V + (long long)(j + 1) * n, n);
+    pass_dispatch(c, PASS_UPD_NRM, w.V, n, nv, w.W, w.V + (long long)(j + 1) * n, n, j);
     arnoldi_reduce<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, nv, c->gdev, 2, j);
     c->launches += 6;
     return cuda_check(c, cudaGetLastError(), "arnoldi");
@@ -331,6 +341,7 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
         cycle_init<<<1, 32, 0, c->stream>>>(c->gdev, dsc + 1, std::min(rel_factor, 1.0), m);
         c->launches++;
         const int jmax = std::min(m, o->max_iters - inf.iters);
+        const size_t prof_first = c->prof_used;
         for (int j = 0; j < jmax; ++j) {
             const double *scale_j = &c->gdev->scale[j];
             double *vj = w.V + (long long)j * n;
@@ -357,6 +368,7 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
         c->launches += 2;
         if ((st = cuda_check(c, cudaGetLastError(), "cycle update")) != LLG_OK) return st;
         if ((st = sync_read(c, gh, c->gdev, GMRES_HEADER_BYTES)) != LLG_OK) return st;
+        prof_discard(c, prof_first, gh->jd);
         inf.iters += gh->jd;
         inf.applies += gh->jd;
         inf.restarts++;

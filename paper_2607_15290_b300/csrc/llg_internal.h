@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string>
 #include <functional>
+#include <vector>
 #include "../../include/llg.h"
 
 namespace llg {
@@ -99,12 +100,25 @@ struct llg_ctx {
     int sync_every = 4;
     long long launches = 0;      // kernels launched through this context
     std::string err;
+    // live per-kernel-class timing (llg_profile_begin/end): one event pair per launch
+    struct ProfEntry { cudaEvent_t a, b; double bytes, flops; int tag; int valid; };
+    int prof_class = 0;
+    std::vector<ProfEntry> prof;
+    size_t prof_used = 0;
+    int prof_open = -1;
 };
 
 namespace llg {
 
 llg_status set_error(llg_ctx *c, llg_status s, const std::string &msg);
 llg_status cuda_check(llg_ctx *c, cudaError_t e, const char *what);
+
+// live profiling of one kernel class: call prof_begin right before a launch and
+// prof_end right after it; both are no-ops unless that class is being profiled.
+enum KClass { K_NONE = 0, K_XFWD = 1, K_AXIS = 2, K_XINV = 3, K_ARNOLDI = 4 };
+void prof_begin(llg_ctx *c, int cls, double bytes, double flops, int tag = -1);
+void prof_end(llg_ctx *c);
+void prof_discard(llg_ctx *c, size_t first, int min_tag);
 
 // spectral.cu
 template <typename T, typename TIn, typename TOut>

@@ -366,6 +366,24 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
     ra.n0 = n0; ra.logn0 = g.logn[0]; ra.S = g.S; ra.G = G;
     ra.rows = g.rows; ra.N = g.N; ra.io = io;
 
+    // algorithmic bytes / flops of each pass (live spectrum only; inputs read and outputs written once)
+    const double W = sizeof(T), CB = 2.0 * sizeof(T), Ti = sizeof(TIn), To = sizeof(TOut);
+    const double Nd = (double)g.N, live = (double)g.rows * (n0 + n0 / 2 + 1);
+    auto fftf = [](double lines, int n, int logn) { return lines * 5.0 * n * logn; };
+    double in_b = 3 * Nd * Ti;
+    if (in_mode == IN_FUSED) in_b = 3 * Nd * W + 4 * Nd * Ti;
+    if (in_mode == IN_NODAL_T) in_b = 3 * Nd * W + 4 * Nd * Ti + Nd * To;
+    double out_b = 0;
+    switch (out_mode) {
+        case OUT_APPLY: out_b = Nd * (3 * W + Ti + 4 * To); break;
+        case OUT_FUSED: out_b = Nd * (3 * W + 3 * Ti + 4 * To); break;
+        case OUT_MATVEC: out_b = Nd * (3 * W + 4 * Ti + 4 * To); break;
+        case OUT_FIELD: out_b = Nd * 4 * To; break;
+        case OUT_PLAIN: out_b = Nd * 3 * To; break;
+        default: out_b = Nd * (4 * Ti + 7 * W + 4 * To); break;
+    }
+    const double xf = fftf(1.5 * g.rows, n0, g.logn[0]);
+
     cudaError_t e;
 #define LLG_DISPATCH_E(FN, MODE)                                                              \
     switch (E) {                                                                              \
@@ -374,7 +392,9 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
         case 8: e = FN<T, TIn, TOut, 8>(c, MODE, ra, blocks, threads, smr); break;            \
         default: e = FN<T, TIn, TOut, 16>(c, MODE, ra, blocks, threads, smr); break;          \
     }
+    prof_begin(c, K_XFWD, in_b + live * CB, xf);
     LLG_DISPATCH_E(launch_row_fwd_E, in_mode)
+    prof_end(c);
     if (e != cudaSuccess) return cuda_check(c, e, "x-pass forward");
     c->launches++;
 
@@ -383,32 +403,41 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
     ca.n0 = n0; ca.S = g.S;
     ca.tx = sig_of<T>(c, sym.exchange, 0);
     ca.sa = (T)sym.a; ca.sb = (T)sym.b; ca.sscale = (T)sym.scale; ca.sinv = sym.invert;
-    const int ntile_by = 8;  // tiles are launched with the plan's TW; S is a multiple of 16
-    (void)ntile_by;
     auto tiles = [&](int nl) { return g.S / col_plan<T>(nl).TW; };
     if (g.dim == 2) {
         ca.tw = tw_of<T>(c, 1); ca.nl = g.n[1]; ca.logn = g.logn[1];
         ca.ls = g.S; ca.bs = 0; ca.tl = sig_of<T>(c, sym.exchange, 1); ca.tb = nullptr;
+        prof_begin(c, K_AXIS, 2 * live * CB, 2 * fftf((double)(n0 + n0 / 2 + 1), g.n[1], g.logn[1]));
         e = launch_col<T>(c, 7, ca, dim3(tiles(g.n[1]), 1));
+        prof_end(c);
         if (e != cudaSuccess) return cuda_check(c, e, "y-pass");
         c->launches++;
     } else {
         ColArgs<T> cy = ca;
         cy.tw = tw_of<T>(c, 1); cy.nl = g.n[1]; cy.logn = g.logn[1];
         cy.ls = g.S; cy.bs = (long long)g.n[1] * g.S; cy.tl = nullptr; cy.tb = nullptr;
+        const double ylines = (double)(n0 + n0 / 2 + 1) * g.n[2], zlines = (double)(n0 + n0 / 2 + 1) * g.n[1];
+        prof_begin(c, K_AXIS, 2 * live * CB, fftf(ylines, g.n[1], g.logn[1]));
         e = launch_col<T>(c, 1, cy, dim3(tiles(g.n[1]), g.n[2]));
+        prof_end(c);
         if (e != cudaSuccess) return cuda_check(c, e, "y-pass forward");
         ColArgs<T> cz = ca;
         cz.tw = tw_of<T>(c, 2); cz.nl = g.n[2]; cz.logn = g.logn[2];
         cz.ls = (long long)g.n[1] * g.S; cz.bs = g.S;
         cz.tl = sig_of<T>(c, sym.exchange, 2); cz.tb = sig_of<T>(c, sym.exchange, 1);
+        prof_begin(c, K_AXIS, 2 * live * CB, 2 * fftf(zlines, g.n[2], g.logn[2]));
         e = launch_col<T>(c, 7, cz, dim3(tiles(g.n[2]), g.n[1]));
+        prof_end(c);
         if (e != cudaSuccess) return cuda_check(c, e, "z-pass");
+        prof_begin(c, K_AXIS, 2 * live * CB, fftf(ylines, g.n[1], g.logn[1]));
         e = launch_col<T>(c, 2, cy, dim3(tiles(g.n[1]), g.n[2]));
+        prof_end(c);
         if (e != cudaSuccess) return cuda_check(c, e, "y-pass inverse");
         c->launches += 3;
     }
+    prof_begin(c, K_XINV, live * CB + out_b, xf);
     LLG_DISPATCH_E(launch_row_inv_E, out_mode)
+    prof_end(c);
 #undef LLG_DISPATCH_E
     if (e != cudaSuccess) return cuda_check(c, e, "x-pass inverse");
     c->launches++;
