@@ -120,6 +120,27 @@ llg_status llg_ffthss_apply(llg_ctx *ctx, const llg_params *prm, const double *m
 /* The same in FP32 (m, p, z float planes). */
 llg_status llg_ffthss_apply_f32(llg_ctx *ctx, const llg_params *prm, const float *m, const float *p,
                                 float *z, int transpose);
+/* Maximum spectral scratch of llg_ffthss_apply_noalloc, in complex FP64 slots (4 MiB):
+   a grid fits when n1 * n2 * S <= this, with S = 1.5 n0 + 1 rounded up to a multiple of 16
+   (for example 256 x 256 or 512 x 256 in 2D, 32^3 or 64 x 64 x 32 in 3D). */
+#define LLG_NOALLOC_MAX_SPECTRAL 262144
+/* The paper has no counterpart to this call: it is llg_ffthss_apply for callers that cannot
+   allocate device memory and therefore cannot create a context -- a time-critical loop that
+   has promised no allocation after start-up, an application whose device memory is fully
+   reserved by another allocator (where an extra cudaMalloc fails or fragments), or a plug-in
+   environment that may not create device allocations.  It calls no cudaMalloc, cudaFree or
+   other allocating routine: its spectral scratch and tables live in one static device array
+   (about 4.1 MiB) that every GPU loading the library holds until the process exits.
+   Same operation, layout and precision as llg_ffthss_apply (FP64; transpose != 0 applies
+   M^{-T}); m, p, z are caller-owned device pointers; cuda_stream is a cudaStream_t (NULL =
+   legacy default stream).  Grids beyond LLG_NOALLOC_MAX_SPECTRAL return
+   LLG_ERR_UNSUPPORTED_SIZE before any launch.  The first call on each device fetches the
+   array's device address (cudaGetSymbolAddress) with that device current; make that first
+   call before any stream capture.  All calls share the array (each rewrites its tables and
+   clears the scratch it uses), so calls that overlap on the GPU -- on other streams or host
+   threads -- race on it and must be serialised by the caller. */
+llg_status llg_ffthss_apply_noalloc(const llg_grid *grid, const llg_params *prm, const double *m,
+                                    const double *p, double *z, int transpose, void *cuda_stream);
 /* Left-preconditioned operator z = M^{-1} A x in one Fourier round trip, using
    (H + lambda I)^{-1} A = I + (H + lambda I)^{-1}(S - lambda I) (consequence of Sec. 3.2's
    splitting; the operator GMRES iterates on).  FP64. */

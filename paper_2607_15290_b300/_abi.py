@@ -29,7 +29,8 @@ PREC_FP64, PREC_FP32_FLEX = 0, 1
 # every symbol the header declares, in declaration order
 EXPORTS = [
     "llg_create", "llg_destroy", "llg_last_error", "llg_set_stream", "llg_launch_count", "llg_nodes",
-    "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_precond_saddle_apply",
+    "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_ffthss_apply_noalloc",
+    "llg_precond_saddle_apply",
     "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy",
     "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate",
 ]
@@ -86,6 +87,7 @@ def lib():
     L.llg_saddle_apply.argtypes = [ctx, P(Params), vp, vp, vp, C.c_int]
     L.llg_ffthss_apply.argtypes = [ctx, P(Params), vp, vp, vp, C.c_int]
     L.llg_ffthss_apply_f32.argtypes = [ctx, P(Params), vp, vp, vp, C.c_int]
+    L.llg_ffthss_apply_noalloc.argtypes = [P(Grid), P(Params), vp, vp, vp, C.c_int, vp]
     L.llg_precond_saddle_apply.argtypes = [ctx, P(Params), vp, vp, vp]
     L.llg_gmres_solve.argtypes = [ctx, P(Params), P(Opts), vp, vp, vp, P(Info)]
     L.llg_step_euler.argtypes = [ctx, P(Params), P(Opts), vp, vp, vp, P(Info)]
