@@ -169,10 +169,15 @@ def main():
     ap.add_argument("--roofline-class", default="arnoldi", choices=["xfwd", "axis", "xinv", "arnoldi"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, apply sweep and e2e legs")
+    ap.add_argument("--apply-sweep", default="", help="only time the isolated FFT-HSS apply on these grids, "
+                    "e.g. '256^3,128^3,1024^2' (one JSON line each, with a per-pass breakdown)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --apply-sweep")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.apply_sweep:
+        return apply_sweep(args)
 
     import numpy as np
     import torch
@@ -385,6 +390,58 @@ def extras_leg(L, I, ctx, prm, w, m0, args):
                  "note": "each step copies m^n host->device, runs the midpoint step cold (no warm start) "
                          "and copies m^{n+1} back"}
     return ex
+
+
+def apply_sweep(args):
+    """Isolated FFT-HSS apply (FP32 or FP64) per grid: time per apply (CUDA events over
+    args.steps applies after args.warmup), algorithmic bytes of the pass plan, and the same
+    split by pass class from the library's live per-launch timing."""
+    import numpy as np
+    import torch
+    import paper_2607_15290_b300 as L
+    from paper_2607_15290_b300 import inputs as I
+    pk = peaks()
+    for spec in args.apply_sweep.split(","):
+        base, dim = spec.split("^")
+        n = (int(base),) * int(dim)
+        N = int(np.prod(n))
+        ctx = L.Context(n)
+        f32 = args.precision == "fp32"
+        dt = torch.float32 if f32 else torch.float64
+        m = torch.tensor(I.smooth3d(n) if len(n) == 3 else I.smooth2d(n), device="cuda").to(dt)
+        p = torch.randn((4,) + tuple(reversed(n)), device="cuda", dtype=dt)
+        z = torch.empty_like(p)
+        prm = L.Params(alpha=0.1, k=workload_params(max(n))["k"], theta=0.5, lam=0.5)
+        fn = (lambda: L.llg_ffthss_apply_f32(ctx, prm, m, p, out=z)) if f32 else \
+             (lambda: L.llg_ffthss_apply(ctx, prm, m, p, out=z))
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        w = 4 if f32 else 8
+        passes = 3 if len(n) == 2 else 5
+        algo = (11 + 6 * (passes - 1)) * w * N
+        out = {"grid": list(n), "precision": args.precision, "ms_per_apply": ms, "applies_per_s": 1e3 / ms,
+               "gbs_algorithmic": algo / ms / 1e6, "frac_of_hbm": algo / ms / 1e6 / pk["hbm_gbs"],
+               "algorithmic_bytes": algo, "passes": passes}
+        for cls in ("xfwd", "axis", "xinv"):
+            ctx.profile_begin(cls)
+            for _ in range(args.steps):
+                fn()
+            r = ctx.profile_end()
+            out[cls] = {"ms_per_apply": r["ms"] / args.steps, "launches_per_apply": r["launches"] / args.steps,
+                        "gbs": r["bytes"] / (r["ms"] / 1e3) / 1e9 if r["ms"] else None,
+                        "gflops": r["flops"] / (r["ms"] / 1e3) / 1e9 if r["ms"] else None}
+        print(json.dumps(out), flush=True)
+        ctx.close()
+        del m, p, z
+        torch.cuda.empty_cache()
 
 
 if __name__ == "__main__":

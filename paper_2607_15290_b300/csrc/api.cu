@@ -96,11 +96,7 @@ __global__ void k_max_partials(const double *__restrict__ partials, int nb, doub
 }
 
 __global__ void k_sum_partials_n(const double *__restrict__ partials, int nb, int cnt, double *dst) {
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += partials[(long long)b * RB_STRIDE + i];
-        dst[i] = s;
-    }
+    block_sum_partials(partials, nb, cnt, dst);
 }
 
 __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, long long n) {
@@ -130,6 +126,25 @@ __global__ void k_euler_update(const double *__restrict__ m, const double *__res
 __global__ void k_axpy3(const double *__restrict__ m, const double *__restrict__ v, double c, double *out, long long n3) {
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x)
         out[e] = m[e] + (v ? c * v[e] : 0.0);
+}
+
+// Picard advance: mhat' = m + hk v, and the exact residual of x for the new blocks,
+// r0 = r_prev - [A(mhat') - A(mhat)] x = r_prev - (dm x v + dm r, -dm . v), dm = mhat' - mhat
+// (only the nodal skew/constraint blocks depend on the midpoint field)
+__global__ void k_picard_advance(const double *__restrict__ m, const double *__restrict__ x, double hk, double *mhat,
+                                 const double *__restrict__ rprev, double *r0, long long N) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        const double v1 = x[j], v2 = x[N + j], v3 = x[2 * N + j], r = x[3 * N + j];
+        const double a1 = m[j] + hk * v1, a2 = m[N + j] + hk * v2, a3 = m[2 * N + j] + hk * v3;
+        const double d1 = a1 - mhat[j], d2 = a2 - mhat[N + j], d3 = a3 - mhat[2 * N + j];
+        r0[j] = rprev[j] - (d2 * v3 - d3 * v2 + d1 * r);
+        r0[N + j] = rprev[N + j] - (d3 * v1 - d1 * v3 + d2 * r);
+        r0[2 * N + j] = rprev[2 * N + j] - (d1 * v2 - d2 * v1 + d3 * r);
+        r0[3 * N + j] = rprev[3 * N + j] + (d1 * v1 + d2 * v2 + d3 * v3);
+        mhat[j] = a1;
+        mhat[N + j] = a2;
+        mhat[2 * N + j] = a3;
+    }
 }
 
 // partial sums of |v - vold|^2 and |v|^2
@@ -337,7 +352,7 @@ llg_status check_nodes(llg_ctx *c, const double *m) {
 
 // solve A(m; theta) x = b with the chosen precision
 llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *o, const double *m, const double *b,
-                 double *x, llg_info *info) {
+                 double *x, llg_info *info, const double *r0 = nullptr) {
     llg_status st = check_nodes(c, m);
     if (st != LLG_OK) return st;
     const bool flex = o->precision == LLG_PREC_FP32_FLEX;
@@ -361,7 +376,7 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
             return spectral_chain<float, float, double>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
         };
     }
-    return gmres_run(c, ops, flex, o, b, x, info);
+    return gmres_run(c, ops, flex, o, b, x, info, r0);
 }
 
 llg_status rhs_velocity(llg_ctx *c, const llg_params *p, const double *m, double *b) {
@@ -382,7 +397,7 @@ llg_status energy_async(llg_ctx *c, const llg_params *p, const double *m, double
     if (st != LLG_OK) return st;
     const int nb = reduction_blocks(c);
     k_energy_partials<<<nb, RB_THREADS, 0, c->stream>>>(m, tmp, p->h_ext[0], p->h_ext[1], p->h_ext[2], c->geo.N, c->red);
-    k_sum_partials_n<<<1, 32, 0, c->stream>>>(c->red, nb, 1, dst_dev);
+    k_sum_partials_n<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, 1, dst_dev);
     c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "energy");
 }
@@ -690,6 +705,7 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
     double *vold = c->aux + 4 * N;     // 3N
     double *mhat = c->aux + 7 * N;     // 3N
     double *tmp = c->aux + 10 * N;     // 4N
+    double *r0 = c->aux + 14 * N;      // 4N
     const int nb = reduction_blocks(c), gb = grid_blocks(c);
     llg_info inf = llg_info();
     if (o->diagnostics) {
@@ -704,9 +720,10 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
     c->launches++;
     llg_status lin_st = LLG_OK;
     bool conv = false;
+    bool have_r0 = false;
     for (int it = 0; it < o->picard_max; ++it) {
         llg_info si = llg_info();
-        st = solve(c, p, 0.5, o, mhat, b, x_out, &si);
+        st = solve(c, p, 0.5, o, mhat, b, x_out, &si, have_r0 ? r0 : nullptr);
         inf.iters += si.iters;
         inf.restarts += si.restarts;
         inf.applies += si.applies;
@@ -716,13 +733,19 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
         else if (st != LLG_OK) { inf.status = st; if (info) *info = inf; return st; }
         if (it >= 1) {
             k_picard_norms<<<nb, RB_THREADS, 0, c->stream>>>(x_out, vold, 3 * N, c->red);
-            k_sum_partials_n<<<1, 32, 0, c->stream>>>(c->red, nb, 2, c->dsc);
+            k_sum_partials_n<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, 2, c->dsc);
             c->launches += 2;
             if ((st = sync_scalars(c, 2)) != LLG_OK) return st;
             if (std::sqrt(c->hsc[0]) <= o->picard_tol * std::sqrt(c->hsc[1])) { conv = true; break; }
         }
         cudaMemcpyAsync(vold, x_out, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
-        k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, 3 * N);
+        if (c->ws.last_res) {
+            k_picard_advance<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, c->ws.last_res, r0, N);
+            have_r0 = true;
+        } else {
+            k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, 3 * N);
+            have_r0 = false;
+        }
         c->launches++;
     }
     k_mid_final<<<nb, RB_THREADS, 0, c->stream>>>(m_n, x_out, p->k, m_next, N, c->red);
@@ -807,7 +830,7 @@ llg_status llg_adjoint_step(llg_ctx *c, const llg_params *p, const llg_opts *o, 
     }
     k_adj_final<<<nb, RB_THREADS, 0, c->stream>>>(mbar_next, y, lapy, x, lapu, p->alpha, p->h_ext[0], p->h_ext[1],
                                                   p->h_ext[2], mbar_n, N, c->red);
-    k_sum_partials_n<<<1, 32, 0, c->stream>>>(c->red, nb, 4, c->dsc);
+    k_sum_partials_n<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, 4, c->dsc);
     c->launches += 2;
     if ((st = cuda_check(c, cudaGetLastError(), "adjoint")) != LLG_OK) return st;
     if ((st = sync_scalars(c, 4)) != LLG_OK) return st;

@@ -73,12 +73,7 @@ __global__ void __launch_bounds__(RB_THREADS) arnoldi_reduce(const double *__res
                                                              GmresDev *gd, int mode, int j) {
     if (gd->done) return;
     __shared__ double tot[64];
-    const int cnt = mode == 2 ? 1 : nv;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += partials[(long long)b * 64 + i];
-        tot[i] = s;
-    }
+    block_sum_partials(partials, nb, mode == 2 ? 1 : nv, tot);
     __syncthreads();
     if (mode == 0) {
         for (int i = threadIdx.x; i < nv; i += blockDim.x) gd->h1[i] = tot[i] * gd->scale[i];
@@ -187,16 +182,10 @@ __global__ void __launch_bounds__(RB_THREADS) dot_partials(const double *__restr
 }
 
 __global__ void sum_partials(const double *__restrict__ partials, int nb, double *dst) {
-    __shared__ double sh[RB_THREADS];
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[(long long)b * 64];
-    sh[threadIdx.x] = s;
+    __shared__ double tot[1];
+    block_sum_partials(partials, nb, 1, tot);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < (int)blockDim.x; ++i) t += sh[i];
-        *dst = t;
-    }
+    if (threadIdx.x == 0) *dst = tot[0];
 }
 
 // ------------------------------------------------------------------ host helpers
@@ -294,10 +283,11 @@ static llg_status sync_read(llg_ctx *c, void *dst_host, const void *src_dev, siz
 }
 
 llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_opts *o, const double *b, double *x,
-                     llg_info *info) {
+                     llg_info *info, const double *r0) {
     llg_status st = ensure_workspace(c, o->restart, flexible);
     if (st != LLG_OK) return st;
     Workspace &w = c->ws;
+    w.last_res = nullptr;
     const long long n = w.n;
     const int m = o->restart;
     double *dsc = c->dsc, *hsc = c->hsc;
@@ -323,7 +313,18 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
         return LLG_OK;
     };
     double rel;
-    if ((st = true_residual(&rel)) != LLG_OK) return st;
+    if (r0) {
+        // the caller's exact initial residual replaces the first matvec
+        double *dst = flexible ? w.V : w.T;
+        cudaError_t ce = cudaMemcpyAsync(dst, r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+        if ((st = cuda_check(c, ce, "initial residual")) != LLG_OK) return st;
+        if ((st = dot_async(c, dst, dst, n, dsc)) != LLG_OK) return st;
+        if ((st = sync_read(c, hsc, dsc, sizeof(double))) != LLG_OK) return st;
+        rel = std::sqrt(hsc[0]) / nb;
+    } else if ((st = true_residual(&rel)) != LLG_OK) {
+        return st;
+    }
+    w.last_res = flexible ? w.V : w.T;
     const double eta = flexible ? 1e-5 : 0.0;
     llg_status result = LLG_OK;
     for (;;) {

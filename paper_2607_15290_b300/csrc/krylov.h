@@ -38,7 +38,10 @@ struct SolveOps {
 };
 
 llg_status ensure_workspace(llg_ctx *c, int restart, bool flexible);
+// r0 (optional, FP64, 4N): the exact initial residual b - A x of the given x, when the
+// caller can form it without a matvec.  On return c->ws.last_res points at the final
+// FP64 true residual b - A x (NULL when b = 0); it stays valid until the next solve.
 llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_opts *o, const double *b, double *x,
-                     llg_info *info);
+                     llg_info *info, const double *r0 = nullptr);
 
 }  // namespace llg

@@ -70,6 +70,7 @@ struct Workspace {
     double *W = nullptr;      // n
     double *T = nullptr;      // n
     double *R = nullptr;      // n
+    const double *last_res = nullptr;   // final true residual of the last solve (T or V_0)
 };
 
 struct GmresDev;   // device-side Arnoldi state (krylov.cu)

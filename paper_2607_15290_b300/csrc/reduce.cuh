@@ -44,6 +44,22 @@ __device__ __forceinline__ void block_max_store(double v, double *out) {
     }
 }
 
+// Sum partials[b * RB_STRIDE + i] over b < nb for i < cnt with the whole block:
+// warp w handles outputs i = w, w + 8, ...; lane l adds blocks l, l + 32, ... in
+// order, then a fixed shuffle tree combines the lanes (deterministic).  The result
+// for output i is returned to lane 0 of its warp through out[i].
+__device__ __forceinline__ void block_sum_partials(const double *__restrict__ partials, int nb, int cnt,
+                                                   double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < cnt; i += nw) {
+        double s = 0.0;
+        for (int b = lane; b < nb; b += 32) s += partials[(long long)b * RB_STRIDE + i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) out[i] = s;
+    }
+}
+
 // chunk [lo, hi) of n elements owned by this block (contiguous)
 __device__ __forceinline__ void block_chunk(long long n, long long &lo, long long &hi) {
     long long per = (n + gridDim.x - 1) / gridDim.x;
