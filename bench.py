@@ -199,6 +199,7 @@ def main():
     ctx = L.Context(n)
     prm = L.Params(alpha=w["alpha"], k=w["k"], theta=0.5, lam=w["lam"], h_ext=w["h"])
     opts = L.Opts(restart=30, rtol=1e-10, precision=L.PREC_FP32_FLEX, picard_tol=1e-10, picard_max=50)
+    tuning = ctx.autotune()           # launch shapes of the axis passes, picked on this device
     m0 = torch.tensor(I.smooth3d(n), device="cuda")
     x = ctx.empty(4)
     mA, mB = m0.clone(), ctx.empty(3)
@@ -291,6 +292,7 @@ def main():
         "gmres_iters_per_solve": iters / max(solves, 1), "max_len_drift": drift,
         "roofline": roof, "gpu_launches": gpu_launches, "clocks": clk,
         "fp64_fma_tflops_measured": fp64_peak, "fp32_fma_tflops_measured": fp32_peak,
+        "autotune": tuning.strip().splitlines(),
     }
     out.update(extras)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -353,6 +355,7 @@ def extras_leg(L, I, ctx, prm, w, m0, args):
     # isolated FP32 FFT-HSS apply: 128^3 (this context) and 256^3
     def apply_rate(c2, nn):
         N = nn[0] * nn[1] * nn[2]
+        c2.autotune(fp64=False, fp32=True)
         mm = torch.tensor(I.smooth3d(nn), device="cuda").float()
         p = torch.randn((4,) + tuple(reversed(nn)), device="cuda", dtype=torch.float32)
         z = torch.empty_like(p)
@@ -406,6 +409,7 @@ def apply_sweep(args):
         n = (int(base),) * int(dim)
         N = int(np.prod(n))
         ctx = L.Context(n)
+        tuning = ctx.autotune(fp64=args.precision == "fp64", fp32=args.precision == "fp32")
         f32 = args.precision == "fp32"
         dt = torch.float32 if f32 else torch.float64
         m = torch.tensor(I.smooth3d(n) if len(n) == 3 else I.smooth2d(n), device="cuda").to(dt)
@@ -429,7 +433,7 @@ def apply_sweep(args):
         algo = (11 + 6 * (passes - 1)) * w * N
         out = {"grid": list(n), "precision": args.precision, "ms_per_apply": ms, "applies_per_s": 1e3 / ms,
                "gbs_algorithmic": algo / ms / 1e6, "frac_of_hbm": algo / ms / 1e6 / pk["hbm_gbs"],
-               "algorithmic_bytes": algo, "passes": passes}
+               "algorithmic_bytes": algo, "passes": passes, "autotune": tuning.strip().splitlines()}
         for cls in ("xfwd", "axis", "xinv"):
             ctx.profile_begin(cls)
             for _ in range(args.steps):

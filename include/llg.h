@@ -183,6 +183,16 @@ llg_status llg_adjoint_step(llg_ctx *ctx, const llg_params *prm, const llg_opts 
    *out is a HOST pointer; synchronises the stream. */
 llg_status llg_energy(llg_ctx *ctx, const llg_params *prm, const double *m, double *out);
 
+/* Autotune the launch shapes of the Fourier axis passes for this context's grid (no
+   counterpart in the paper): every compiled shape (register kernel with 4/8/16-column
+   tiles; shared-memory-staged FP32 kernel with several tile/sub-batch sizes) is run on a
+   deterministic spectrum, its result checked against the default shape (candidates that
+   disagree beyond 1e-4 FP32 / 1e-11 FP64 relative are rejected), timed with CUDA events, and
+   the fastest kept for each pass.  precision_mask: 1 = FP64 passes, 2 = FP32 passes, 3 = both.
+   report (HOST, may be NULL): text of the timings and choices.  Allocates and frees scratch;
+   synchronises the stream.  Without this call the default shapes are used. */
+llg_status llg_autotune(llg_ctx *ctx, int precision_mask, char *report, int report_len);
+
 /* ---------------------------------------------------------------- measurement support
    (infrastructure for the benchmark; no counterpart in the paper) */
 

@@ -105,6 +105,14 @@ class Context:
     def launches(self):
         return int(self.lib.llg_launch_count(self.h))
 
+    def autotune(self, fp64=True, fp32=True):
+        """Pick the fastest valid launch shape of every Fourier axis pass for this grid;
+        returns the tuner's report (timings per candidate and the choices)."""
+        buf = C.create_string_buffer(8192)
+        mask = (1 if fp64 else 0) | (2 if fp32 else 0)
+        self._check(self.lib.llg_autotune(self.h, mask, buf, len(buf)))
+        return buf.value.decode()
+
     def profile_begin(self, kernel_class):
         """Time every launch of one kernel class ('xfwd', 'axis', 'xinv', 'arnoldi') live."""
         self._check(self.lib.llg_profile_begin(self.h, _abi.KCLASS[kernel_class]))

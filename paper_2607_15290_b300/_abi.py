@@ -32,7 +32,7 @@ EXPORTS = [
     "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_ffthss_apply_noalloc",
     "llg_precond_saddle_apply",
     "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy",
-    "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate",
+    "llg_autotune", "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate",
 ]
 KCLASS = {"xfwd": 1, "axis": 2, "xinv": 3, "arnoldi": 4}
 
@@ -94,6 +94,7 @@ def lib():
     L.llg_step_midpoint.argtypes = [ctx, P(Params), P(Opts), vp, vp, vp, vp, P(Info)]
     L.llg_adjoint_step.argtypes = [ctx, P(Params), P(Opts), vp, vp, vp, vp, d, d, P(Info)]
     L.llg_energy.argtypes = [ctx, P(Params), vp, d]
+    L.llg_autotune.argtypes = [ctx, C.c_int, C.c_char_p, C.c_int]
     L.llg_profile_begin.argtypes = [ctx, C.c_int]
     L.llg_profile_end.argtypes = [ctx, d, P(C.c_longlong), d, d]
     L.llg_probe_fma_rate.argtypes = [ctx, C.c_int, d]

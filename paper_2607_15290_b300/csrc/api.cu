@@ -512,6 +512,20 @@ llg_status llg_destroy(llg_ctx *c) {
 
 const char *llg_last_error(const llg_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
+llg_status llg_autotune(llg_ctx *c, int precision_mask, char *report, int report_len) {
+    LLG_GUARD(c);
+    if (precision_mask < 1 || precision_mask > 3) return set_error(c, LLG_ERR_INVALID_ARG, "precision_mask must be 1, 2 or 3");
+    llg_status st = ensure_spec(c, (precision_mask & 1) != 0, (precision_mask & 2) != 0);
+    if (st != LLG_OK) return st;
+    std::string rep;
+    st = llg::autotune(c, precision_mask, &rep);
+    if (report && report_len > 0) {
+        std::strncpy(report, rep.c_str(), (size_t)report_len - 1);
+        report[report_len - 1] = 0;
+    }
+    return st;
+}
+
 llg_status llg_profile_begin(llg_ctx *c, int kernel_class) {
     LLG_GUARD(c);
     if (kernel_class < LLG_KCLASS_NONE || kernel_class > LLG_KCLASS_ARNOLDI)

@@ -26,9 +26,9 @@ enum { PASS_DOT = 0, PASS_UPD_DOT = 1, PASS_UPD_NRM = 2 };
 
 template <int MAXV, int MODE>
 __global__ void __launch_bounds__(RB_THREADS) arnoldi_pass(const double *__restrict__ V, long long ldv, int nv,
-                                                           const GmresDev *__restrict__ gd,
-                                                           const double *win, double *wout, long long n,
-                                                           double *__restrict__ partials) {
+                                                                const GmresDev *__restrict__ gd,
+                                                                const double *win, double *wout, long long n,
+                                                                double *__restrict__ partials) {
     if (gd->done) return;
     __shared__ double coef[MAXV];
     if (threadIdx.x < nv) {
@@ -44,9 +44,14 @@ __global__ void __launch_bounds__(RB_THREADS) arnoldi_pass(const double *__restr
     for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
         double w = win[e];
         if (MODE == PASS_DOT) {
+            // all basis loads of this element first, then the multiply-adds: the loads
+            // must be in flight together, or the FP64 pipe waits on memory latency
+            double vv[MAXV];
+#pragma unroll
+            for (int i = 0; i < MAXV; ++i) vv[i] = (i < nv) ? __ldg(&V[i * ldv + e]) : 0.0;
 #pragma unroll
             for (int i = 0; i < MAXV; ++i)
-                if (i < nv) acc[i] += __ldg(&V[i * ldv + e]) * w;
+                if (i < nv) acc[i] += vv[i] * w;
         } else {
             double vv[MAXV];
 #pragma unroll

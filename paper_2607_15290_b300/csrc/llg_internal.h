@@ -75,6 +75,15 @@ struct Workspace {
 
 struct GmresDev;   // device-side Arnoldi state (krylov.cu)
 
+// launch shape of an axis pass: kind 0 = register kernel (E elements per thread, TW
+// columns per block); kind 1 = staged kernel (TW = tile columns, CB = columns per
+// compute sub-batch, E = 8)
+struct ColCfg {
+    int kind, E, TW, CB;
+};
+// axis-pass slots: 2D y pass; 3D y forward, z (with multiplier), y inverse
+enum { SLOT_2D = 0, SLOT_Y_FWD = 1, SLOT_Z = 2, SLOT_Y_INV = 3, NSLOT = 4 };
+
 }  // namespace llg
 
 struct llg_ctx {
@@ -100,6 +109,8 @@ struct llg_ctx {
     int sm_count = 148;
     int sync_every = 4;
     long long launches = 0;      // kernels launched through this context
+    llg::ColCfg colcfg[2][llg::NSLOT];   // [FP32, FP64][slot] axis-pass shapes
+    bool tuned[2] = {false, false};      // set by llg_autotune
     std::string err;
     // live per-kernel-class timing (llg_profile_begin/end): one event pair per launch
     struct ProfEntry { cudaEvent_t a, b; double bytes, flops; int tag; int valid; };
@@ -122,6 +133,7 @@ void prof_end(llg_ctx *c);
 void prof_discard(llg_ctx *c, size_t first, int min_tag);
 
 // spectral.cu
+llg_status autotune(llg_ctx *c, int prec_mask, std::string *report);
 template <typename T, typename TIn, typename TOut>
 llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<TIn, TOut, T> &io,
                           const Symbol &sym);

@@ -120,12 +120,11 @@ cudaError_t launch_cols_ETW(int mode, const ColArgs<double> &a, dim3 grid, cudaS
 
 cudaError_t launch_cols(int mode, const ColArgs<double> &a, dim3 grid, cudaStream_t st) {
     const ColPlan p = col_plan<double>(a.nl);
-    switch (p.E) {
-        case 2: return launch_cols_ETW<2, 8>(mode, a, grid, st);
-        case 4: return launch_cols_ETW<4, 8>(mode, a, grid, st);
-        case 8: return launch_cols_ETW<8, 8>(mode, a, grid, st);
-        default: return launch_cols_ETW<16, 8>(mode, a, grid, st);
-    }
+    if (p.E == 2 && p.TW == 8) return launch_cols_ETW<2, 8>(mode, a, grid, st);
+    if (p.E == 4 && p.TW == 8) return launch_cols_ETW<4, 8>(mode, a, grid, st);
+    if (p.E == 8 && p.TW == 8) return launch_cols_ETW<8, 8>(mode, a, grid, st);
+    if (p.E == 8 && p.TW == 4) return launch_cols_ETW<8, 4>(mode, a, grid, st);
+    return cudaErrorInvalidValue;
 }
 
 bool pow2_ok(int n) { return n >= 2 && n <= 1024 && (n & (n - 1)) == 0; }
@@ -173,7 +172,7 @@ extern "C" llg_status llg_ffthss_apply_noalloc(const llg_grid *grid, const llg_p
                          (int)std::lround(std::log2((double)n[2]))};
 
     // x-passes: same launch shape as the context path
-    const int E = row_E(n[0]), P = n[0] / E;
+    const int E = row_E<double>(n[0]), P = n[0] / E;
     const long long pairs = rows / 2;
     int G = 256 / (3 * P);
     if (G < 1) G = 1;
@@ -195,8 +194,7 @@ extern "C" llg_status llg_ffthss_apply_noalloc(const llg_grid *grid, const llg_p
         switch (E) {
             case 2: return launch_rows<2>(fwd, transpose != 0, ra, blocks, threads, smr, stream);
             case 4: return launch_rows<4>(fwd, transpose != 0, ra, blocks, threads, smr, stream);
-            case 8: return launch_rows<8>(fwd, transpose != 0, ra, blocks, threads, smr, stream);
-            default: return launch_rows<16>(fwd, transpose != 0, ra, blocks, threads, smr, stream);
+            default: return launch_rows<8>(fwd, transpose != 0, ra, blocks, threads, smr, stream);
         }
     };
     auto tiles = [&](int nl) { return S / col_plan<double>(nl).TW; };

@@ -15,6 +15,10 @@
 // Because the multiplier is real and even, the operator maps real fields to real
 // fields and is complex-linear, so c1 and c2 share one complex transform; c3 is
 // transformed two rows at a time and stored as a half spectrum.
+#include <vector>
+#include <string>
+#include <cstdio>
+#include <algorithm>
 #include "spectral_kernels.cuh"
 
 namespace llg {
@@ -84,14 +88,116 @@ static cudaError_t launch_col_ETW(llg_ctx *c, int mode, const ColArgs<T> &a, dim
     return cudaErrorInvalidValue;
 }
 
+template <int TWL, int CB>
+static cudaError_t launch_staged_TW(llg_ctx *c, int mode, const ColArgs<float> &a, int live, int batches) {
+    constexpr int SROW = StagedRow<TWL>::value;
+    const size_t sm = (size_t)a.nl * SROW * sizeof(float2);
+    const int threads = CB * (a.nl / 8);
+    const dim3 grid((live + TWL - 1) / TWL, batches);
+#define LLG_CS(MODE)                                                                          \
+    case MODE: {                                                                              \
+        auto k = col_staged_kernel<8, TWL, CB, MODE>;                                         \
+        cudaError_t e = set_smem(k, sm);                                                      \
+        if (e != cudaSuccess) return e;                                                       \
+        k<<<grid, threads, sm, c->stream>>>(a, live);                                         \
+        return cudaGetLastError();                                                            \
+    }
+    switch (mode) {
+        LLG_CS(1) LLG_CS(2) LLG_CS(7)
+    }
+#undef LLG_CS
+    return cudaErrorInvalidValue;
+}
+
+// the staged shapes that are compiled: (tile columns, columns per sub-batch)
+static const int kStaged[][2] = {{64, 64}, {64, 32}, {64, 16}, {32, 32}, {32, 16}, {32, 8},
+                                 {16, 16}, {16, 8},  {16, 4},  {8, 8},   {8, 4}};
+
+static cudaError_t launch_staged(llg_ctx *c, int mode, const ColArgs<float> &a, int live, int batches, int TWL, int CB) {
+#define LLG_ST(X, Y) if (TWL == X && CB == Y) return launch_staged_TW<X, Y>(c, mode, a, live, batches);
+    LLG_ST(64, 64) LLG_ST(64, 32) LLG_ST(64, 16) LLG_ST(32, 32) LLG_ST(32, 16) LLG_ST(32, 8)
+    LLG_ST(16, 16) LLG_ST(16, 8) LLG_ST(16, 4) LLG_ST(8, 8) LLG_ST(8, 4)
+#undef LLG_ST
+    return cudaErrorInvalidValue;
+}
+
+template <typename T> static int col_E(int nl) { return (sizeof(T) == 4 && nl >= 1024) ? 16 : (nl >= 8 ? 8 : nl); }
+
+// every launch shape the tuner may pick for a line length
+template <typename T> static std::vector<ColCfg> col_candidates(int nl) {
+    std::vector<ColCfg> v;
+    const int E = col_E<T>(nl);
+    const int tws[] = {4, 8, 16};
+    for (int TW : tws) {
+        if (sizeof(T) == 4 && TW == 4) continue;
+        if (sizeof(T) == 8 && TW == 16) continue;
+        if (TW * (nl / E) > 512) continue;
+        if ((size_t)nl * TW * sizeof(cplx<T>) > 200 * 1024) continue;
+        v.push_back({0, E, TW, 0});
+    }
+    if (sizeof(T) == 4 && nl >= 64) {
+        for (auto &sc : kStaged) {
+            const int TWL = sc[0], CB = sc[1];
+            const int srow = TWL + ((8 - (TWL & 15)) & 15);
+            if (CB * (nl / 8) > 512 || CB * (nl / 8) < 64) continue;
+            if ((size_t)nl * srow * sizeof(float2) > 160 * 1024) continue;
+            v.push_back({1, 8, TWL, CB});
+        }
+    }
+    return v;
+}
+
+// untuned default: the register kernel with the widest tile that fits 512 threads
+template <typename T> static ColCfg col_default(int nl) {
+    const ColPlan p = col_plan<T>(nl);
+    return {0, p.E, p.TW, 0};
+}
+
 template <typename T>
-static cudaError_t launch_col(llg_ctx *c, int mode, const ColArgs<T> &a, dim3 grid) {
-    ColPlan p = col_plan<T>(a.nl);
-#define LLG_CE(EE, TT) if (p.E == EE && p.TW == TT) return launch_col_ETW<T, EE, TT>(c, mode, a, grid);
-    LLG_CE(2, 8) LLG_CE(4, 8) LLG_CE(8, 8) LLG_CE(16, 8)
-    LLG_CE(2, 16) LLG_CE(4, 16) LLG_CE(8, 16) LLG_CE(16, 16)
+static cudaError_t launch_col_cfg(llg_ctx *c, int mode, const ColArgs<T> &a, int batches, const ColCfg &cfg) {
+    if (cfg.kind == 1) {
+        if constexpr (sizeof(T) == 4) return launch_staged(c, mode, a, a.n0 + a.n0 / 2 + 1, batches, cfg.TW, cfg.CB);
+        return cudaErrorInvalidValue;
+    }
+    const dim3 grid(a.S / cfg.TW, batches);
+#define LLG_CE(EE, TT) if (cfg.E == EE && cfg.TW == TT) return launch_col_ETW<T, EE, TT>(c, mode, a, grid);
+    if constexpr (sizeof(T) == 8) {
+        LLG_CE(2, 8) LLG_CE(4, 8) LLG_CE(8, 8) LLG_CE(2, 4) LLG_CE(4, 4) LLG_CE(8, 4)
+    } else {
+        LLG_CE(2, 16) LLG_CE(4, 16) LLG_CE(8, 16) LLG_CE(16, 16) LLG_CE(2, 8) LLG_CE(4, 8) LLG_CE(8, 8) LLG_CE(16, 8)
+    }
 #undef LLG_CE
     return cudaErrorInvalidValue;
+}
+
+template <typename T> static ColCfg slot_cfg(llg_ctx *c, int slot, int nl) {
+    const int pi = sizeof(T) == 4 ? 0 : 1;
+    return c->tuned[pi] ? c->colcfg[pi][slot] : col_default<T>(nl);
+}
+
+// column arguments of one axis-pass slot, with a given multiplier
+template <typename T>
+static void slot_args(llg_ctx *c, int slot, const Symbol &sym, ColArgs<T> &ca, int &batches, int &mode) {
+    const SpecGeom &g = c->geo;
+    ca.spec = spec_of<T>(c);
+    ca.n0 = g.n[0]; ca.S = g.S;
+    ca.tx = sig_of<T>(c, sym.exchange, 0);
+    ca.sa = (T)sym.a; ca.sb = (T)sym.b; ca.sscale = (T)sym.scale; ca.sinv = sym.invert;
+    ca.tl = nullptr; ca.tb = nullptr;
+    if (slot == SLOT_2D) {
+        ca.tw = tw_of<T>(c, 1); ca.nl = g.n[1]; ca.logn = g.logn[1]; ca.ls = g.S; ca.bs = 0;
+        ca.tl = sig_of<T>(c, sym.exchange, 1);
+        batches = 1; mode = 7;
+    } else if (slot == SLOT_Z) {
+        ca.tw = tw_of<T>(c, 2); ca.nl = g.n[2]; ca.logn = g.logn[2];
+        ca.ls = (long long)g.n[1] * g.S; ca.bs = g.S;
+        ca.tl = sig_of<T>(c, sym.exchange, 2); ca.tb = sig_of<T>(c, sym.exchange, 1);
+        batches = g.n[1]; mode = 7;
+    } else {
+        ca.tw = tw_of<T>(c, 1); ca.nl = g.n[1]; ca.logn = g.logn[1];
+        ca.ls = g.S; ca.bs = (long long)g.n[1] * g.S;
+        batches = g.n[2]; mode = slot == SLOT_Y_FWD ? 1 : 2;
+    }
 }
 
 template <typename T, typename TIn, typename TOut>
@@ -99,7 +205,7 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
                           const Symbol &sym) {
     const SpecGeom &g = c->geo;
     const int n0 = g.n[0];
-    const int E = row_E(n0), P = n0 / E;
+    const int E = row_E<T>(n0), P = n0 / E;
     const long long pairs = g.rows / 2;
     int G = 256 / (3 * P);
     if (G < 1) G = 1;
@@ -139,7 +245,10 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
         case 2: e = FN<T, TIn, TOut, 2>(c, MODE, ra, blocks, threads, smr); break;            \
         case 4: e = FN<T, TIn, TOut, 4>(c, MODE, ra, blocks, threads, smr); break;            \
         case 8: e = FN<T, TIn, TOut, 8>(c, MODE, ra, blocks, threads, smr); break;            \
-        default: e = FN<T, TIn, TOut, 16>(c, MODE, ra, blocks, threads, smr); break;          \
+        default:                                                                              \
+            if constexpr (sizeof(T) == 4) e = FN<T, TIn, TOut, 16>(c, MODE, ra, blocks, threads, smr); \
+            else e = cudaErrorInvalidValue;                                                   \
+            break;                                                                            \
     }
     prof_begin(c, K_XFWD, in_b + live * CB, xf);
     LLG_DISPATCH_E(launch_row_fwd_E, in_mode)
@@ -147,42 +256,25 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
     if (e != cudaSuccess) return cuda_check(c, e, "x-pass forward");
     c->launches++;
 
-    ColArgs<T> ca;
-    ca.spec = spec_of<T>(c);
-    ca.n0 = n0; ca.S = g.S;
-    ca.tx = sig_of<T>(c, sym.exchange, 0);
-    ca.sa = (T)sym.a; ca.sb = (T)sym.b; ca.sscale = (T)sym.scale; ca.sinv = sym.invert;
-    auto tiles = [&](int nl) { return g.S / col_plan<T>(nl).TW; };
-    if (g.dim == 2) {
-        ca.tw = tw_of<T>(c, 1); ca.nl = g.n[1]; ca.logn = g.logn[1];
-        ca.ls = g.S; ca.bs = 0; ca.tl = sig_of<T>(c, sym.exchange, 1); ca.tb = nullptr;
-        prof_begin(c, K_AXIS, 2 * live * CB, 2 * fftf((double)(n0 + n0 / 2 + 1), g.n[1], g.logn[1]));
-        e = launch_col<T>(c, 7, ca, dim3(tiles(g.n[1]), 1));
+    const double livec = (double)(n0 + n0 / 2 + 1);
+    auto run_slot = [&](int slot, double flops) -> cudaError_t {
+        ColArgs<T> ca;
+        int batches = 1, mode = 7;
+        slot_args<T>(c, slot, sym, ca, batches, mode);
+        prof_begin(c, K_AXIS, 2 * live * CB, flops);
+        cudaError_t err = launch_col_cfg<T>(c, mode, ca, batches, slot_cfg<T>(c, slot, ca.nl));
         prof_end(c);
-        if (e != cudaSuccess) return cuda_check(c, e, "y-pass");
         c->launches++;
+        return err;
+    };
+    if (g.dim == 2) {
+        e = run_slot(SLOT_2D, 2 * fftf(livec, g.n[1], g.logn[1]));
+        if (e != cudaSuccess) return cuda_check(c, e, "y-pass");
     } else {
-        ColArgs<T> cy = ca;
-        cy.tw = tw_of<T>(c, 1); cy.nl = g.n[1]; cy.logn = g.logn[1];
-        cy.ls = g.S; cy.bs = (long long)g.n[1] * g.S; cy.tl = nullptr; cy.tb = nullptr;
-        const double ylines = (double)(n0 + n0 / 2 + 1) * g.n[2], zlines = (double)(n0 + n0 / 2 + 1) * g.n[1];
-        prof_begin(c, K_AXIS, 2 * live * CB, fftf(ylines, g.n[1], g.logn[1]));
-        e = launch_col<T>(c, 1, cy, dim3(tiles(g.n[1]), g.n[2]));
-        prof_end(c);
-        if (e != cudaSuccess) return cuda_check(c, e, "y-pass forward");
-        ColArgs<T> cz = ca;
-        cz.tw = tw_of<T>(c, 2); cz.nl = g.n[2]; cz.logn = g.logn[2];
-        cz.ls = (long long)g.n[1] * g.S; cz.bs = g.S;
-        cz.tl = sig_of<T>(c, sym.exchange, 2); cz.tb = sig_of<T>(c, sym.exchange, 1);
-        prof_begin(c, K_AXIS, 2 * live * CB, 2 * fftf(zlines, g.n[2], g.logn[2]));
-        e = launch_col<T>(c, 7, cz, dim3(tiles(g.n[2]), g.n[1]));
-        prof_end(c);
-        if (e != cudaSuccess) return cuda_check(c, e, "z-pass");
-        prof_begin(c, K_AXIS, 2 * live * CB, fftf(ylines, g.n[1], g.logn[1]));
-        e = launch_col<T>(c, 2, cy, dim3(tiles(g.n[1]), g.n[2]));
-        prof_end(c);
-        if (e != cudaSuccess) return cuda_check(c, e, "y-pass inverse");
-        c->launches += 3;
+        const double ylines = livec * g.n[2], zlines = livec * g.n[1];
+        if ((e = run_slot(SLOT_Y_FWD, fftf(ylines, g.n[1], g.logn[1]))) != cudaSuccess) return cuda_check(c, e, "y-pass forward");
+        if ((e = run_slot(SLOT_Z, 2 * fftf(zlines, g.n[2], g.logn[2]))) != cudaSuccess) return cuda_check(c, e, "z-pass");
+        if ((e = run_slot(SLOT_Y_INV, fftf(ylines, g.n[1], g.logn[1]))) != cudaSuccess) return cuda_check(c, e, "y-pass inverse");
     }
     prof_begin(c, K_XINV, live * CB + out_b, xf);
     LLG_DISPATCH_E(launch_row_inv_E, out_mode)
@@ -191,6 +283,135 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
     if (e != cudaSuccess) return cuda_check(c, e, "x-pass inverse");
     c->launches++;
     return LLG_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+
+// deterministic pseudo-random fill in [-1, 1) (hash of the index)
+template <typename C>
+__global__ void k_fill_pattern(C *p, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ull;
+        h ^= h >> 29; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 32;
+        const double a = (double)(h & 0xFFFFFF) / 8388608.0 - 1.0, b = (double)((h >> 24) & 0xFFFFFF) / 8388608.0 - 1.0;
+        p[i].x = (decltype(p[i].x))a;
+        p[i].y = (decltype(p[i].y))b;
+    }
+}
+
+// per-block max |a - b| and max |b| over the live columns of every spectral row
+template <typename C>
+__global__ void k_live_maxdiff(const C *a, const C *b, long long rows, int S, int live, double *partials) {
+    double d = 0.0, m = 0.0;
+    const long long n = rows * live;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / live, col = i % live, k = r * S + col;
+        d = fmax(d, fmax(fabs((double)a[k].x - (double)b[k].x), fabs((double)a[k].y - (double)b[k].y)));
+        m = fmax(m, fmax(fabs((double)b[k].x), fabs((double)b[k].y)));
+    }
+    __shared__ double sd[256], sm2[256];
+    sd[threadIdx.x] = d;
+    sm2[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 1; t < (int)blockDim.x; ++t) { d = fmax(d, sd[t]); m = fmax(m, sm2[t]); }
+        partials[2 * blockIdx.x] = d;
+        partials[2 * blockIdx.x + 1] = m;
+    }
+}
+
+static std::string cfg_name(const ColCfg &f) {
+    char b[64];
+    if (f.kind == 0) snprintf(b, sizeof b, "register(E%d,TW%d)", f.E, f.TW);
+    else snprintf(b, sizeof b, "staged(TW%d,CB%d)", f.TW, f.CB);
+    return b;
+}
+
+template <typename T>
+static llg_status tune_prec(llg_ctx *c, std::string *report) {
+    using C = cplx<T>;
+    const SpecGeom &g = c->geo;
+    const int pi = sizeof(T) == 4 ? 0 : 1;
+    const long long elems = g.rows * (long long)g.S;
+    const int live = g.n[0] + g.n[0] / 2 + 1;
+    C *pristine = nullptr, *ref = nullptr;
+    double *part = nullptr, hp[2 * 512];
+    cudaError_t e = cudaMalloc(&pristine, sizeof(C) * elems);
+    if (e == cudaSuccess) e = cudaMalloc(&ref, sizeof(C) * elems);
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 2 * 512);
+    auto cleanup = [&]() { cudaFree(pristine); cudaFree(ref); cudaFree(part); };
+    if (e != cudaSuccess) { cleanup(); return cuda_check(c, e, "autotune buffers"); }
+    k_fill_pattern<<<512, 256, 0, c->stream>>>(pristine, elems);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<int> slots = g.dim == 2 ? std::vector<int>{SLOT_2D} : std::vector<int>{SLOT_Y_FWD, SLOT_Z, SLOT_Y_INV};
+    static const char *slot_names[] = {"y(2D)", "y-forward", "z", "y-inverse"};
+    llg_status st = LLG_OK;
+    for (int slot : slots) {
+        ColArgs<T> ca;
+        int batches = 1, mode = 7;
+        Symbol sym{1.0, 1e-3, 1.0, 1, 0};
+        slot_args<T>(c, slot, sym, ca, batches, mode);
+        ca.sscale = (T)(1.0 / ca.nl);
+        const ColCfg def = col_default<T>(ca.nl);
+        auto run_once = [&](const ColCfg &f, float *ms) -> cudaError_t {
+            cudaMemcpyAsync(ca.spec, pristine, sizeof(C) * elems, cudaMemcpyDeviceToDevice, c->stream);
+            cudaEventRecord(e0, c->stream);
+            cudaError_t err = launch_col_cfg<T>(c, mode, ca, batches, f);
+            cudaEventRecord(e1, c->stream);
+            if (err != cudaSuccess) return err;
+            err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess && ms) err = cudaEventElapsedTime(ms, e0, e1);
+            return err;
+        };
+        if ((e = run_once(def, nullptr)) != cudaSuccess) { st = cuda_check(c, e, "autotune reference"); break; }
+        cudaMemcpyAsync(ref, ca.spec, sizeof(C) * elems, cudaMemcpyDeviceToDevice, c->stream);
+        ColCfg best = def;
+        float best_ms = 1e30f;
+        char line[256];
+        snprintf(line, sizeof line, "%s slot %s (n=%d):", sizeof(T) == 4 ? "fp32" : "fp64", slot_names[slot], ca.nl);
+        std::string rep = line;
+        for (const ColCfg &f : col_candidates<T>(ca.nl)) {
+            if ((e = run_once(f, nullptr)) != cudaSuccess) { cudaGetLastError(); rep += " " + cfg_name(f) + "=launch-fail"; continue; }
+            k_live_maxdiff<C><<<512, 256, 0, c->stream>>>(ca.spec, ref, g.rows, g.S, live, part);
+            cudaMemcpy(hp, part, sizeof(double) * 2 * 512, cudaMemcpyDeviceToHost);
+            double d = 0, m = 0;
+            for (int b = 0; b < 512; ++b) { d = std::max(d, hp[2 * b]); m = std::max(m, hp[2 * b + 1]); }
+            const double tol = sizeof(T) == 4 ? 1e-4 : 1e-11;
+            if (!(d <= tol * m)) { rep += " " + cfg_name(f) + "=rejected"; continue; }
+            float tot = 0.f, ms = 0.f;
+            for (int r = 0; r < 5; ++r) {
+                if ((e = run_once(f, &ms)) != cudaSuccess) break;
+                tot += ms;
+            }
+            if (e != cudaSuccess) { cudaGetLastError(); continue; }
+            tot /= 5.f;
+            snprintf(line, sizeof line, " %s=%.1fus", cfg_name(f).c_str(), tot * 1e3f);
+            rep += line;
+            if (tot < best_ms) { best_ms = tot; best = f; }
+        }
+        c->colcfg[pi][slot] = best;
+        *report += rep + " -> " + cfg_name(best) + "\n";
+    }
+    // slots the grid does not use keep the default
+    if (g.dim == 2) {
+        for (int sl = 1; sl < NSLOT; ++sl) c->colcfg[pi][sl] = col_default<T>(sl == SLOT_Z ? g.n[2] : g.n[1]);
+    } else {
+        c->colcfg[pi][SLOT_2D] = col_default<T>(g.n[1]);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cleanup();
+    if (st == LLG_OK) c->tuned[pi] = true;
+    return st;
+}
+
+llg_status autotune(llg_ctx *c, int prec_mask, std::string *report) {
+    llg_status st = LLG_OK;
+    if ((prec_mask & 2) && c->spec32) st = tune_prec<float>(c, report);
+    if (st == LLG_OK && (prec_mask & 1) && c->spec64) st = tune_prec<double>(c, report);
+    return st;
 }
 
 template llg_status spectral_chain<double, double, double>(llg_ctx *, int, int, const NodalIO<double, double, double> &, const Symbol &);

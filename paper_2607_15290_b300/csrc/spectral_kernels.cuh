@@ -42,46 +42,71 @@ __global__ void __launch_bounds__(512) row_fwd_kernel(RowArgs<T, TIn, TOut> a) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
-    const int n0 = a.n0, P = n0 / E, LS = RowLayout::size(n0);
+    constexpr int LE = E >= 16 ? 4 : (E >= 8 ? 3 : (E >= 4 ? 2 : 1));
+    const int n0 = a.n0, ln0 = a.logn0, P = n0 >> LE, lP = ln0 - LE, LS = RowLayout::size(n0);
     const long long N = a.N, npairs = a.rows / 2, pair0 = (long long)blockIdx.x * a.G;
     const NodalIO<TIn, TOut, T> &io = a.io;
     const T s = in_scale(io);
 
-    // prologue: node-parallel, coalesced plane loads, staged into shared memory
-    for (int idx = threadIdx.x; idx < 2 * a.G * n0; idx += blockDim.x) {
-        const int gp = idx / (2 * n0), rr = (idx / n0) & 1, xx = idx % n0;
-        const long long pair = pair0 + gp;
-        if (pair >= npairs) continue;
-        const long long j = (2 * pair + rr) * n0 + xx;
-        T u1, u2, u3;
-        if constexpr (IN == IN_V) {
-            u1 = s * (T)io.x[j];
-            u2 = s * (T)io.x[N + j];
-            u3 = s * (T)io.x[2 * N + j];
-        } else if constexpr (IN == IN_M) {
-            u1 = (T)io.x[j];
-            u2 = (T)io.x[N + j];
-            u3 = (T)io.x[2 * N + j];
-        } else if constexpr (IN == IN_FUSED) {
-            const T m1 = io.m[j], m2 = io.m[N + j], m3 = io.m[2 * N + j];
-            const T v1 = s * (T)io.x[j], v2 = s * (T)io.x[N + j], v3 = s * (T)io.x[2 * N + j];
-            const T r = s * (T)io.x[3 * N + j];
-            u1 = m2 * v3 - m3 * v2 + m1 * r - io.lam * v1;
-            u2 = m3 * v1 - m1 * v3 + m2 * r - io.lam * v2;
-            u3 = m1 * v2 - m2 * v1 + m3 * r - io.lam * v3;
-        } else {  // IN_NODAL_T
-            const T m1 = io.m[j], m2 = io.m[N + j], m3 = io.m[2 * N + j];
-            T z4;
-            nodal_inverse<T, true>(m1, m2, m3, io.lam, s * (T)io.x[j], s * (T)io.x[N + j],
-                                   s * (T)io.x[2 * N + j], s * (T)io.x[3 * N + j], u1, u2, u3, z4);
-            io.y[3 * N + j] = (TOut)(z4 / io.lam);
+    // prologue: node-parallel, coalesced plane loads, staged into shared memory.
+    // Loads of KC nodes per thread are issued before any arithmetic so that enough
+    // bytes are in flight to cover the memory latency.
+    constexpr int KC = sizeof(T) == 4 ? 6 : 3;
+    constexpr bool NEED_M = (IN == IN_FUSED || IN == IN_NODAL_T);
+    constexpr int NX = (IN == IN_FUSED || IN == IN_NODAL_T) ? 4 : 3;
+    const int total = 2 * a.G * n0;
+    for (int base = threadIdx.x; base < total; base += KC * blockDim.x) {
+        TIn xv[KC][NX];
+        T mv[KC][3];
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int idx = base + k * blockDim.x;
+            const int gp = idx >> (ln0 + 1), rr = (idx >> ln0) & 1, xx = idx & (n0 - 1);
+            if (idx < total && pair0 + gp < npairs) {
+                const long long j = (2 * (pair0 + gp) + rr) * n0 + xx;
+#pragma unroll
+                for (int q = 0; q < NX; ++q) xv[k][q] = io.x[q * N + j];
+                if constexpr (NEED_M) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) mv[k][q] = io.m[q * N + j];
+                }
+            }
         }
-        sm[(3 * gp + rr) * LS + RowLayout::idx(xx, 1)] = cmk<C>(u1, u2);
-        reinterpret_cast<T *>(&sm[(3 * gp + 2) * LS + RowLayout::idx(xx, 1)])[rr] = u3;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int idx = base + k * blockDim.x;
+            const int gp = idx >> (ln0 + 1), rr = (idx >> ln0) & 1, xx = idx & (n0 - 1);
+            if (!(idx < total && pair0 + gp < npairs)) continue;
+            const long long j = (2 * (pair0 + gp) + rr) * n0 + xx;
+            T u1, u2, u3;
+            if constexpr (IN == IN_V) {
+                u1 = s * (T)xv[k][0];
+                u2 = s * (T)xv[k][1];
+                u3 = s * (T)xv[k][2];
+            } else if constexpr (IN == IN_M) {
+                u1 = (T)xv[k][0];
+                u2 = (T)xv[k][1];
+                u3 = (T)xv[k][2];
+            } else if constexpr (IN == IN_FUSED) {
+                const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];
+                const T v1 = s * (T)xv[k][0], v2 = s * (T)xv[k][1], v3 = s * (T)xv[k][2];
+                const T r = s * (T)xv[k][3];
+                u1 = m2 * v3 - m3 * v2 + m1 * r - io.lam * v1;
+                u2 = m3 * v1 - m1 * v3 + m2 * r - io.lam * v2;
+                u3 = m1 * v2 - m2 * v1 + m3 * r - io.lam * v3;
+            } else {  // IN_NODAL_T
+                T z4;
+                nodal_inverse<T, true>(mv[k][0], mv[k][1], mv[k][2], io.lam, s * (T)xv[k][0], s * (T)xv[k][1],
+                                       s * (T)xv[k][2], s * (T)xv[k][3], u1, u2, u3, z4);
+                io.y[3 * N + j] = (TOut)(z4 / io.lam);
+            }
+            sm[(3 * gp + rr) * LS + RowLayout::idx(xx, 1)] = cmk<C>(u1, u2);
+            reinterpret_cast<T *>(&sm[(3 * gp + 2) * LS + RowLayout::idx(xx, 1)])[rr] = u3;
+        }
     }
     __syncthreads();
 
-    const int line = threadIdx.x / P, t = threadIdx.x % P;
+    const int line = threadIdx.x >> lP, t = threadIdx.x & (P - 1);
     const int gp = line / 3, kind = line % 3;
     const long long pair = pair0 + gp;
     const bool valid = pair < npairs;
@@ -116,7 +141,7 @@ __global__ void __launch_bounds__(512) row_fwd_kernel(RowArgs<T, TIn, TOut> a) {
 // ------------------------------------------------------------------ axis passes
 
 template <typename T, int E, int TW, int MODE>   // MODE bit 1: forward, bit 2: inverse, 4: multiplier
-__global__ void __launch_bounds__(512) col_kernel(ColArgs<T> a) {
+__global__ void __launch_bounds__(512, (sizeof(T) == 4 && E <= 8) ? 2 : 1) col_kernel(ColArgs<T> a) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
@@ -146,6 +171,87 @@ __global__ void __launch_bounds__(512) col_kernel(ColArgs<T> a) {
     for (int q = 0; q < E; ++q) base[(long long)(t + P * q) * a.ls] = v[q];
 }
 
+// ------------------------------------------------------------------ staged FP32 axis pass
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// shared-memory row stride of a staged tile: TWL complex plus padding so that
+// consecutive rows start half a bank cycle apart (conflict-free column reads)
+template <int TWL> struct StagedRow { static constexpr int value = TWL + ((8 - (TWL & 15)) & 15); };
+
+// FP32 axis pass over a tile of TWL adjacent spectral columns: the whole tile
+// (nl rows x TWL complex) is copied into shared memory with asynchronous 16-byte
+// copies (all in flight at once, no registers held), transformed CB columns at a
+// time, and written back with 16-byte stores.  Only columns < live are touched.
+template <int E, int TWL, int CB, int MODE>
+__global__ void __launch_bounds__(512) col_staged_kernel(ColArgs<float> a, int live) {
+    using C = float2;
+    constexpr int SROW = StagedRow<TWL>::value;
+    constexpr int CPR = TWL / 2;   // 16-byte chunks per tile row
+    constexpr int LE = E >= 8 ? 3 : (E >= 4 ? 2 : 1);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const int nl = a.nl, P = nl >> LE;
+    const int col0 = blockIdx.x * TWL;
+    C *g = a.spec + (long long)blockIdx.y * a.bs + col0;
+    const int total = nl * CPR;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int e = q / CPR, cc = q % CPR;
+        if (col0 + 2 * cc < live) cp_async16(&sm[e * SROW + 2 * cc], g + (long long)e * a.ls + 2 * cc);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int c = threadIdx.x % CB, t = threadIdx.x / CB;
+    for (int b = 0; b < TWL / CB; ++b) {
+        const int cl = b * CB + c, col = col0 + cl;
+        C v[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) v[q] = sm[(t + P * q) * SROW + cl];
+        if (MODE & 1) line_fft<E, -1, ColLayout>(v, sm + cl, SROW, nl, a.logn, t, P, a.tw);
+        if (MODE & 4) {
+            const int hn = a.n0 / 2;
+            const bool lv = col <= a.n0 + hn;
+            const float sx = lv ? a.tx[col < a.n0 ? col : col - a.n0] : 0.f;
+            const float sb = a.tb ? a.tb[blockIdx.y] : 0.f;
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const float sig = sx + a.tl[t + P * q] + sb;
+                const float d = a.sa + a.sb * sig;
+                const float mult = lv ? (a.sinv ? a.sscale / d : a.sscale * d) : 0.f;
+                v[q] = cscale(v[q], mult);
+            }
+        }
+        if (MODE & 2) line_fft<E, +1, ColLayout>(v, sm + cl, SROW, nl, a.logn, t, P, a.tw);
+#pragma unroll
+        for (int q = 0; q < E; ++q) sm[(t + P * q) * SROW + cl] = v[q];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int e = q / CPR, cc = q % CPR;
+        if (col0 + 2 * cc < live)
+            *reinterpret_cast<float4 *>(g + (long long)e * a.ls + 2 * cc) =
+                *reinterpret_cast<const float4 *>(&sm[e * SROW + 2 * cc]);
+    }
+}
+
+// staged plan for an FP32 line length: (TWL, CB); E = 8; 512 threads; nl >= 64
+struct StagedPlan { int TWL, CB; };
+static inline StagedPlan staged_plan(int nl) {
+    switch (nl) {
+        case 64: return {64, 64};
+        case 128: return {64, 32};
+        case 256: return {32, 16};
+        case 512: return {16, 8};
+        default: return {8, 4};
+    }
+}
+
 // ------------------------------------------------------------------ x-pass inverse
 
 template <typename T, typename TIn, typename TOut, int E, int OUT>
@@ -153,9 +259,10 @@ __global__ void __launch_bounds__(512) row_inv_kernel(RowArgs<T, TIn, TOut> a) {
     using C = cplx<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
-    const int n0 = a.n0, P = n0 / E, LS = RowLayout::size(n0), hn = n0 / 2;
+    constexpr int LE = E >= 16 ? 4 : (E >= 8 ? 3 : (E >= 4 ? 2 : 1));
+    const int n0 = a.n0, ln0 = a.logn0, P = n0 >> LE, lP = ln0 - LE, LS = RowLayout::size(n0), hn = n0 / 2;
     const long long N = a.N, npairs = a.rows / 2, pair0 = (long long)blockIdx.x * a.G;
-    const int line = threadIdx.x / P, t = threadIdx.x % P;
+    const int line = threadIdx.x >> lP, t = threadIdx.x & (P - 1);
     const int gp = line / 3, kind = line % 3;
     const long long pair = pair0 + gp;
     const bool valid = pair < npairs;
@@ -188,74 +295,119 @@ __global__ void __launch_bounds__(512) row_inv_kernel(RowArgs<T, TIn, TOut> a) {
 
     const NodalIO<TIn, TOut, T> &io = a.io;
     const T s = in_scale(io);
-    for (int idx = threadIdx.x; idx < 2 * a.G * n0; idx += blockDim.x) {
-        const int gq = idx / (2 * n0), rr = (idx / n0) & 1, xx = idx % n0;
-        const long long pr = pair0 + gq;
-        if (pr >= npairs) continue;
-        const long long j = (2 * pr + rr) * n0 + xx;
-        const C w12 = sm[(3 * gq + rr) * LS + RowLayout::idx(xx, 1)];
-        const T w1 = w12.x, w2 = w12.y;
-        const T w3 = reinterpret_cast<const T *>(&sm[(3 * gq + 2) * LS + RowLayout::idx(xx, 1)])[rr];
-        TOut *y = io.y;
-        if constexpr (OUT == OUT_APPLY) {
-            const T m1 = io.m[j], m2 = io.m[N + j], m3 = io.m[2 * N + j];
-            T z1, z2, z3, z4;
-            nodal_inverse<T, false>(m1, m2, m3, io.lam, w1, w2, w3, s * (T)io.x[3 * N + j] / io.lam,
-                                    z1, z2, z3, z4);
-            y[j] = (TOut)z1; y[N + j] = (TOut)z2; y[2 * N + j] = (TOut)z3; y[3 * N + j] = (TOut)z4;
-        } else if constexpr (OUT == OUT_FUSED) {
-            const T m1 = io.m[j], m2 = io.m[N + j], m3 = io.m[2 * N + j];
-            const T v1 = s * (T)io.x[j], v2 = s * (T)io.x[N + j], v3 = s * (T)io.x[2 * N + j];
-            T z1, z2, z3, z4;
-            nodal_inverse<T, false>(m1, m2, m3, io.lam, v1 + w1, v2 + w2, v3 + w3,
-                                    -(m1 * v1 + m2 * v2 + m3 * v3) / io.lam, z1, z2, z3, z4);
-            y[j] = (TOut)z1; y[N + j] = (TOut)z2; y[2 * N + j] = (TOut)z3; y[3 * N + j] = (TOut)z4;
-        } else if constexpr (OUT == OUT_MATVEC) {
-            const T m1 = io.m[j], m2 = io.m[N + j], m3 = io.m[2 * N + j];
-            const T v1 = s * (T)io.x[j], v2 = s * (T)io.x[N + j], v3 = s * (T)io.x[2 * N + j];
-            const T r = s * (T)io.x[3 * N + j];
-            const T sg = io.transpose ? (T)-1 : (T)1;
-            y[j] = (TOut)(w1 + sg * (m2 * v3 - m3 * v2 + m1 * r));
-            y[N + j] = (TOut)(w2 + sg * (m3 * v1 - m1 * v3 + m2 * r));
-            y[2 * N + j] = (TOut)(w3 + sg * (m1 * v2 - m2 * v1 + m3 * r));
-            y[3 * N + j] = (TOut)(-sg * (m1 * v1 + m2 * v2 + m3 * v3));
-        } else if constexpr (OUT == OUT_FIELD) {
-            y[j] = (TOut)(w1 + io.fld[0]);
-            y[N + j] = (TOut)(w2 + io.fld[1]);
-            y[2 * N + j] = (TOut)(w3 + io.fld[2]);
-            y[3 * N + j] = (TOut)0;
-        } else if constexpr (OUT == OUT_PLAIN) {
-            y[j] = (TOut)w1; y[N + j] = (TOut)w2; y[2 * N + j] = (TOut)w3;
-        } else {  // OUT_JT: (J^T y)_v = w - m^n x y_v + (k/2) r y_v - m^{n+1} y_r ; (J^T y)_r = mhat . y_v
-            const T a1 = s * (T)io.x[j], a2 = s * (T)io.x[N + j], a3 = s * (T)io.x[2 * N + j];
-            const T ar = s * (T)io.x[3 * N + j];
-            const T n1 = io.mn[j], n2 = io.mn[N + j], n3 = io.mn[2 * N + j];
-            const T f1 = io.vf[j], f2 = io.vf[N + j], f3 = io.vf[2 * N + j], fr = io.vf[3 * N + j];
-            const T hk = io.half_k;
-            const T p1 = n1 + 2 * hk * f1, p2 = n2 + 2 * hk * f2, p3 = n3 + 2 * hk * f3;  // m^{n+1}
-            const T h1 = n1 + hk * f1, h2 = n2 + hk * f2, h3 = n3 + hk * f3;              // mhat
-            y[j] = (TOut)(w1 - (n2 * a3 - n3 * a2) + hk * fr * a1 - p1 * ar);
-            y[N + j] = (TOut)(w2 - (n3 * a1 - n1 * a3) + hk * fr * a2 - p2 * ar);
-            y[2 * N + j] = (TOut)(w3 - (n1 * a2 - n2 * a1) + hk * fr * a3 - p3 * ar);
-            y[3 * N + j] = (TOut)(h1 * a1 + h2 * a2 + h3 * a3);
+    // epilogue: node-parallel; the plane loads of KC nodes are issued first
+    constexpr int KC = sizeof(T) == 4 ? 6 : 3;
+    constexpr bool NEED_M = (OUT == OUT_APPLY || OUT == OUT_FUSED || OUT == OUT_MATVEC || OUT == OUT_JT);
+    constexpr int XLO = OUT == OUT_APPLY ? 3 : 0;
+    constexpr int XHI = (OUT == OUT_APPLY || OUT == OUT_MATVEC || OUT == OUT_JT) ? 4 : (OUT == OUT_FUSED ? 3 : 0);
+    constexpr bool NEED_F = OUT == OUT_JT;
+    const int total = 2 * a.G * n0;
+    for (int base = threadIdx.x; base < total; base += KC * blockDim.x) {
+        T mv[KC][3];
+        TIn xv[KC][4];
+        T fv[KC][4];
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int idx = base + k * blockDim.x;
+            const int gq = idx >> (ln0 + 1), rr = (idx >> ln0) & 1, xx = idx & (n0 - 1);
+            if (idx < total && pair0 + gq < npairs) {
+                const long long j = (2 * (pair0 + gq) + rr) * n0 + xx;
+                if constexpr (NEED_M) {
+                    const T *mp = OUT == OUT_JT ? io.mn : io.m;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) mv[k][q] = mp[q * N + j];
+                }
+#pragma unroll
+                for (int q = XLO; q < XHI; ++q) xv[k][q] = io.x[q * N + j];
+                if constexpr (NEED_F) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) fv[k][q] = io.vf[q * N + j];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const int idx = base + k * blockDim.x;
+            const int gq = idx >> (ln0 + 1), rr = (idx >> ln0) & 1, xx = idx & (n0 - 1);
+            if (!(idx < total && pair0 + gq < npairs)) continue;
+            const long long j = (2 * (pair0 + gq) + rr) * n0 + xx;
+            const C w12 = sm[(3 * gq + rr) * LS + RowLayout::idx(xx, 1)];
+            const T w1 = w12.x, w2 = w12.y;
+            const T w3 = reinterpret_cast<const T *>(&sm[(3 * gq + 2) * LS + RowLayout::idx(xx, 1)])[rr];
+            TOut *y = io.y;
+            if constexpr (OUT == OUT_APPLY) {
+                T z1, z2, z3, z4;
+                nodal_inverse<T, false>(mv[k][0], mv[k][1], mv[k][2], io.lam, w1, w2, w3,
+                                        s * (T)xv[k][3] / io.lam, z1, z2, z3, z4);
+                y[j] = (TOut)z1; y[N + j] = (TOut)z2; y[2 * N + j] = (TOut)z3; y[3 * N + j] = (TOut)z4;
+            } else if constexpr (OUT == OUT_FUSED) {
+                const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];
+                const T v1 = s * (T)xv[k][0], v2 = s * (T)xv[k][1], v3 = s * (T)xv[k][2];
+                T z1, z2, z3, z4;
+                nodal_inverse<T, false>(m1, m2, m3, io.lam, v1 + w1, v2 + w2, v3 + w3,
+                                        -(m1 * v1 + m2 * v2 + m3 * v3) / io.lam, z1, z2, z3, z4);
+                y[j] = (TOut)z1; y[N + j] = (TOut)z2; y[2 * N + j] = (TOut)z3; y[3 * N + j] = (TOut)z4;
+            } else if constexpr (OUT == OUT_MATVEC) {
+                const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];
+                const T v1 = s * (T)xv[k][0], v2 = s * (T)xv[k][1], v3 = s * (T)xv[k][2];
+                const T r = s * (T)xv[k][3];
+                const T sg = io.transpose ? (T)-1 : (T)1;
+                y[j] = (TOut)(w1 + sg * (m2 * v3 - m3 * v2 + m1 * r));
+                y[N + j] = (TOut)(w2 + sg * (m3 * v1 - m1 * v3 + m2 * r));
+                y[2 * N + j] = (TOut)(w3 + sg * (m1 * v2 - m2 * v1 + m3 * r));
+                y[3 * N + j] = (TOut)(-sg * (m1 * v1 + m2 * v2 + m3 * v3));
+            } else if constexpr (OUT == OUT_FIELD) {
+                y[j] = (TOut)(w1 + io.fld[0]);
+                y[N + j] = (TOut)(w2 + io.fld[1]);
+                y[2 * N + j] = (TOut)(w3 + io.fld[2]);
+                y[3 * N + j] = (TOut)0;
+            } else if constexpr (OUT == OUT_PLAIN) {
+                y[j] = (TOut)w1; y[N + j] = (TOut)w2; y[2 * N + j] = (TOut)w3;
+            } else {  // OUT_JT: (J^T y)_v = w - m^n x y_v + (k/2) r y_v - m^{n+1} y_r ; (J^T y)_r = mhat . y_v
+                const T a1 = s * (T)xv[k][0], a2 = s * (T)xv[k][1], a3 = s * (T)xv[k][2];
+                const T ar = s * (T)xv[k][3];
+                const T n1 = mv[k][0], n2 = mv[k][1], n3 = mv[k][2];
+                const T f1 = fv[k][0], f2 = fv[k][1], f3 = fv[k][2], fr = fv[k][3];
+                const T hk = io.half_k;
+                const T p1 = n1 + 2 * hk * f1, p2 = n2 + 2 * hk * f2, p3 = n3 + 2 * hk * f3;  // m^{n+1}
+                const T h1 = n1 + hk * f1, h2 = n2 + hk * f2, h3 = n3 + hk * f3;              // mhat
+                y[j] = (TOut)(w1 - (n2 * a3 - n3 * a2) + hk * fr * a1 - p1 * ar);
+                y[N + j] = (TOut)(w2 - (n3 * a1 - n1 * a3) + hk * fr * a2 - p2 * ar);
+                y[2 * N + j] = (TOut)(w3 - (n1 * a2 - n2 * a1) + hk * fr * a3 - p3 * ar);
+                y[3 * N + j] = (TOut)(h1 * a1 + h2 * a2 + h3 * a3);
+            }
         }
     }
 }
 
-static inline int row_E(int n0) { return n0 >= 1024 ? 16 : (n0 >= 8 ? 8 : n0); }
+// elements per thread of a line: 8 (16 for 1024-point FP32 lines); FP64 stays at 8 so
+// that its registers do not spill
+template <typename T> static inline int row_E(int n0) {
+    return (sizeof(T) == 4 && n0 >= 1024) ? 16 : (n0 >= 8 ? 8 : n0);
+}
 
+// column tiles: TW adjacent columns (16 FP32 / 8 FP64 complex = 128 B rows), narrowed
+// until the block has at most 512 threads
 struct ColPlan { int E, TW; };
 template <typename T> static inline ColPlan col_plan(int nl) {
-    int E = nl >= 1024 ? 16 : (nl >= 8 ? 8 : nl);
-    int twmax = sizeof(T) == 8 ? 8 : 16;
-    int TW = twmax;
-    while (TW > 8 && TW * (nl / E) > 512) TW >>= 1;
+    const int E = (sizeof(T) == 4 && nl >= 1024) ? 16 : (nl >= 8 ? 8 : nl);
+    int TW = sizeof(T) == 8 ? 8 : 16;
+    while (TW > 4 && TW * (nl / E) > 512) TW >>= 1;
     return {E, TW};
 }
 
+// Dynamic shared-memory limit and the maximum shared-memory carveout, set once per
+// kernel (the carveout keeps shared memory from limiting the resident blocks).
 template <typename K> static inline cudaError_t set_smem(K kern, size_t bytes) {
-    if (bytes > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return cudaSuccess;
+    static thread_local const void *done[256];
+    static thread_local int ndone = 0;
+    for (int i = 0; i < ndone; ++i)
+        if (done[i] == (const void *)kern) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess && ndone < 256) done[ndone++] = (const void *)kern;
+    (void)bytes;
+    return e;
 }
 
 }  // namespace llg

@@ -227,3 +227,23 @@ def test_error_statuses(dev):
     # the context stays usable after errors
     x, info = L.llg_gmres_solve(ctx, pl, L.Opts(), gpu(m), gpu(b))
     assert info["status"] == 0
+
+
+@pytest.mark.parametrize("n", [(64, 32, 64), (256, 16), (16, 128, 128)])
+def test_autotuned_shapes_keep_parity(dev, n):
+    """After llg_autotune picks launch shapes (staged or register axis passes), FP64 and FP32
+    applies still match the oracle at the usual tolerances."""
+    og = O.Grid(n)
+    ctx = L.Context(n)
+    report = ctx.autotune()
+    assert "->" in report
+    m = I.random_unit(n, seed=112)
+    p = I.random_saddle_vector(n, seed=113)
+    po, pl = prm_pair(alpha=0.1, k=1e-4, theta=0.5)
+    ref = O.ffthss_apply(og, po, m, p)
+    got = host(L.llg_ffthss_apply(ctx, pl, gpu(m), gpu(p)))
+    assert rel(got, ref) <= 1e-12
+    got32 = host(L.llg_ffthss_apply_f32(ctx, pl, gpu(m, torch.float32), gpu(p, torch.float32)))
+    assert rel(got32, ref) <= 2e-5
+    ref_t = O.saddle_apply(og, po, m, p, transpose=True)
+    assert rel(host(L.llg_saddle_apply(ctx, pl, gpu(m), gpu(p), transpose=True)), ref_t) <= 1e-12
