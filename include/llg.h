@@ -183,6 +183,41 @@ llg_status llg_adjoint_step(llg_ctx *ctx, const llg_params *prm, const llg_opts 
    *out is a HOST pointer; synchronises the stream. */
 llg_status llg_energy(llg_ctx *ctx, const llg_params *prm, const double *m, double *out);
 
+/* ---------------------------------------------------------------- ensembles
+   Many independent 2D problems advanced together by projected-Euler steps (Sec. 2.4, 3.2)
+   in ONE persistent cooperative kernel launch, captured in a CUDA graph when the stream
+   allows capture (spec batching; the paper solves one problem at a time).  Every
+   problem has its own grid, damping, time step and field; all advance through the same
+   phases in lockstep (right-hand side; flexible GMRES(restart) with the FP32 FFT--HSS
+   application and inner matvec, FP64 Arnoldi and least squares; FP64 true residual; the
+   Euler update) with per-problem convergence flags, so converged problems idle. */
+typedef struct {
+    int n[2];          /* grid n0 x n1, each 128, 256 or 512 */
+    double L[2];       /* cell lengths */
+    llg_params prm;    /* alpha, c_ex, k, lambda, h_ext, exchange (theta is 1: Euler) */
+    double *m;         /* device, 3 planes: m^0 on entry, m after the steps on return */
+    double *x;         /* device, 4 planes: on return (v | r) of the last step */
+} llg_problem;
+typedef struct llg_ensemble llg_ensemble;
+/* Allocate the per-problem workspace (Krylov bases, spectra) and descriptors.  opts: restart
+   (1..31), max_iters per solve, rtol (FP64 true residual); precision is always FP32-flexible.
+   cuda_stream: a cudaStream_t (a non-default stream allows graph capture). */
+llg_status llg_ensemble_create(const llg_problem *probs, int count, const llg_opts *opts, void *cuda_stream,
+                               llg_ensemble **out);
+/* Run `steps` Euler steps of every problem in one launch (synchronises).  infos (HOST, count
+   entries, caller order, may be NULL): iterations and cycles summed over the steps, worst
+   final relative residual, worst status.  used_graph (HOST, may be NULL): 1 if the launch ran
+   as a captured CUDA graph. */
+llg_status llg_ensemble_run(llg_ensemble *ens, int steps, llg_info *infos, int *used_graph);
+/* Number of persistent blocks (must not exceed llg_ensemble_max_blocks, the co-resident limit). */
+llg_status llg_ensemble_set_blocks(llg_ensemble *ens, int blocks);
+int llg_ensemble_max_blocks(const llg_ensemble *ens);
+/* Pick the persistent block count by timing one step for each multiple of the SM count up to
+   the co-resident limit (problems' m restored afterwards); *blocks (HOST) receives the choice. */
+llg_status llg_ensemble_autotune(llg_ensemble *ens, int *blocks);
+llg_status llg_ensemble_destroy(llg_ensemble *ens);
+const char *llg_ensemble_last_error(const llg_ensemble *ens);
+
 /* Autotune the launch shapes of the Fourier axis passes for this context's grid (no
    counterpart in the paper): every compiled shape (register kernel with 4/8/16-column
    tiles; shared-memory-staged FP32 kernel with several tile/sub-batch sizes) is run on a

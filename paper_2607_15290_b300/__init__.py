@@ -22,7 +22,7 @@ from ._abi import EX_FD2, EX_SPECTRAL, PREC_FP32_FLEX, PREC_FP64
 __all__ = [
     "LLGError", "Params", "Opts", "Context", "EX_SPECTRAL", "EX_FD2", "PREC_FP64", "PREC_FP32_FLEX",
     "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_precond_saddle_apply",
-    "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy",
+    "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy", "Ensemble",
 ]
 
 
@@ -236,6 +236,64 @@ def llg_adjoint_step(ctx: Context, prm: Params, opts: Opts, m_n, x, mbar_next, m
                                   ctx._arr(mbar_next, 3), ctx._arr(mbar_n, 3), C.byref(da), dh, C.byref(info))
     ctx._check(st, info.as_dict())
     return mbar_n, da.value, [dh[0], dh[1], dh[2]], info.as_dict()
+
+
+class Ensemble:
+    """Independent 2D problems advanced together by projected-Euler steps in one persistent
+    launch (llg_ensemble_*).  problems: list of dicts with keys n (n0, n1), L, params (Params),
+    m (3, n1, n0) float64 CUDA tensor (updated in place) and x (4, n1, n0) output tensor."""
+
+    def __init__(self, problems, opts: Opts, stream=None):
+        torch = _torch()
+        self.lib = _abi.lib()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (_abi.Problem * len(problems))()
+        for q, p in zip(arr, problems):
+            q.n[0], q.n[1] = p["n"]
+            q.L[0], q.L[1] = p.get("L", (1.0, 1.0))
+            q.prm = p["params"].c()
+            for key, comps in (("m", 3), ("x", 4)):
+                t = p[key]
+                if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                        and tuple(t.shape) == (comps, p["n"][1], p["n"][0])):
+                    raise ValueError(f"problem {key}: expected a contiguous float64 CUDA tensor of shape "
+                                     f"{(comps, p['n'][1], p['n'][0])}")
+            q.m = p["m"].data_ptr()
+            q.x = p["x"].data_ptr()
+        self.count = len(problems)
+        h = C.c_void_p()
+        st = self.lib.llg_ensemble_create(arr, len(problems), C.byref(opts.c()), C.c_void_p(self.stream.cuda_stream),
+                                          C.byref(h))
+        if st != 0:
+            raise LLGError(st, "llg_ensemble_create failed")
+        self.h = h
+
+    def autotune(self):
+        b = C.c_int()
+        st = self.lib.llg_ensemble_autotune(self.h, C.byref(b))
+        if st != 0:
+            raise LLGError(st, self.lib.llg_ensemble_last_error(self.h).decode())
+        return b.value
+
+    def run(self, steps):
+        """Returns (infos in caller order, used_graph)."""
+        infos = (_abi.Info * self.count)()
+        g = C.c_int()
+        st = self.lib.llg_ensemble_run(self.h, steps, infos, C.byref(g))
+        if st not in (0, 3):
+            raise LLGError(st, self.lib.llg_ensemble_last_error(self.h).decode())
+        return [i.as_dict() for i in infos], bool(g.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.llg_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def llg_energy(ctx: Context, prm: Params, m):

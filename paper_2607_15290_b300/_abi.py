@@ -32,6 +32,8 @@ EXPORTS = [
     "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_ffthss_apply_noalloc",
     "llg_precond_saddle_apply",
     "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy",
+    "llg_ensemble_create", "llg_ensemble_run", "llg_ensemble_set_blocks", "llg_ensemble_max_blocks",
+    "llg_ensemble_autotune", "llg_ensemble_destroy", "llg_ensemble_last_error",
     "llg_autotune", "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate",
 ]
 KCLASS = {"xfwd": 1, "axis": 2, "xinv": 3, "arnoldi": 4}
@@ -49,6 +51,10 @@ class Params(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("restart", C.c_int), ("max_iters", C.c_int), ("rtol", C.c_double), ("precision", C.c_int),
                 ("picard_max", C.c_int), ("picard_tol", C.c_double), ("diagnostics", C.c_int)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("n", C.c_int * 2), ("L", C.c_double * 2), ("prm", Params), ("m", C.c_void_p), ("x", C.c_void_p)]
 
 
 class Info(C.Structure):
@@ -95,11 +101,19 @@ def lib():
     L.llg_adjoint_step.argtypes = [ctx, P(Params), P(Opts), vp, vp, vp, vp, d, d, P(Info)]
     L.llg_energy.argtypes = [ctx, P(Params), vp, d]
     L.llg_autotune.argtypes = [ctx, C.c_int, C.c_char_p, C.c_int]
+    L.llg_ensemble_create.argtypes = [P(Problem), C.c_int, P(Opts), vp, P(vp)]
+    L.llg_ensemble_run.argtypes = [vp, C.c_int, P(Info), P(C.c_int)]
+    L.llg_ensemble_set_blocks.argtypes = [vp, C.c_int]
+    L.llg_ensemble_max_blocks.argtypes = [vp]
+    L.llg_ensemble_autotune.argtypes = [vp, P(C.c_int)]
+    L.llg_ensemble_destroy.argtypes = [vp]
+    L.llg_ensemble_last_error.argtypes = [vp]
+    L.llg_ensemble_last_error.restype = C.c_char_p
     L.llg_profile_begin.argtypes = [ctx, C.c_int]
     L.llg_profile_end.argtypes = [ctx, d, P(C.c_longlong), d, d]
     L.llg_probe_fma_rate.argtypes = [ctx, C.c_int, d]
     for name in EXPORTS:
-        if name not in ("llg_last_error", "llg_launch_count", "llg_nodes"):
+        if name not in ("llg_last_error", "llg_launch_count", "llg_nodes", "llg_ensemble_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -37,14 +37,17 @@ __device__ __forceinline__ T in_scale(const NodalIO<TIn, TOut, T> &io) {
 
 // ------------------------------------------------------------------ x-pass forward
 
+// Body of the forward x-pass for row-pair group `bidx`, run by the first `nthr`
+// threads of the block (the remaining threads, if any, only take part in the
+// barriers and work on spare shared-memory lines).
 template <typename T, typename TIn, typename TOut, int E, int IN>
-__global__ void __launch_bounds__(512) row_fwd_kernel(RowArgs<T, TIn, TOut> a) {
+__device__ __forceinline__ void row_fwd_body(const RowArgs<T, TIn, TOut> &a, long long bidx, int nthr, unsigned char *smraw) {
     using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
+    const int tid = threadIdx.x;
     constexpr int LE = E >= 16 ? 4 : (E >= 8 ? 3 : (E >= 4 ? 2 : 1));
     const int n0 = a.n0, ln0 = a.logn0, P = n0 >> LE, lP = ln0 - LE, LS = RowLayout::size(n0);
-    const long long N = a.N, npairs = a.rows / 2, pair0 = (long long)blockIdx.x * a.G;
+    const long long N = a.N, npairs = a.rows / 2, pair0 = bidx * a.G;
     const NodalIO<TIn, TOut, T> &io = a.io;
     const T s = in_scale(io);
 
@@ -55,12 +58,12 @@ __global__ void __launch_bounds__(512) row_fwd_kernel(RowArgs<T, TIn, TOut> a) {
     constexpr bool NEED_M = (IN == IN_FUSED || IN == IN_NODAL_T);
     constexpr int NX = (IN == IN_FUSED || IN == IN_NODAL_T) ? 4 : 3;
     const int total = 2 * a.G * n0;
-    for (int base = threadIdx.x; base < total; base += KC * blockDim.x) {
+    for (int base = tid; tid < nthr && base < total; base += KC * nthr) {
         TIn xv[KC][NX];
         T mv[KC][3];
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-            const int idx = base + k * blockDim.x;
+            const int idx = base + k * nthr;
             const int gp = idx >> (ln0 + 1), rr = (idx >> ln0) & 1, xx = idx & (n0 - 1);
             if (idx < total && pair0 + gp < npairs) {
                 const long long j = (2 * (pair0 + gp) + rr) * n0 + xx;
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(512) row_fwd_kernel(RowArgs<T, TIn, TOut> a) {
         }
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-            const int idx = base + k * blockDim.x;
+            const int idx = base + k * nthr;
             const int gp = idx >> (ln0 + 1), rr = (idx >> ln0) & 1, xx = idx & (n0 - 1);
             if (!(idx < total && pair0 + gp < npairs)) continue;
             const long long j = (2 * (pair0 + gp) + rr) * n0 + xx;
@@ -106,10 +109,10 @@ __global__ void __launch_bounds__(512) row_fwd_kernel(RowArgs<T, TIn, TOut> a) {
     }
     __syncthreads();
 
-    const int line = threadIdx.x >> lP, t = threadIdx.x & (P - 1);
+    const int line = tid >> lP, t = tid & (P - 1);
     const int gp = line / 3, kind = line % 3;
     const long long pair = pair0 + gp;
-    const bool valid = pair < npairs;
+    const bool valid = gp < a.G && pair < npairs;
     C v[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = sm[line * LS + RowLayout::idx(t + P * q, 1)];
@@ -138,17 +141,23 @@ __global__ void __launch_bounds__(512) row_fwd_kernel(RowArgs<T, TIn, TOut> a) {
     }
 }
 
+template <typename T, typename TIn, typename TOut, int E, int IN>
+__global__ void __launch_bounds__(512) row_fwd_kernel(RowArgs<T, TIn, TOut> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    row_fwd_body<T, TIn, TOut, E, IN>(a, blockIdx.x, blockDim.x, smraw);
+}
+
 // ------------------------------------------------------------------ axis passes
 
+// Body of an axis pass for column tile bx of batch by (TW * nl / E threads).
 template <typename T, int E, int TW, int MODE>   // MODE bit 1: forward, bit 2: inverse, 4: multiplier
-__global__ void __launch_bounds__(512, (sizeof(T) == 4 && E <= 8) ? 2 : 1) col_kernel(ColArgs<T> a) {
+__device__ __forceinline__ void col_body(const ColArgs<T> &a, int bx, int by, unsigned char *smraw) {
     using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
     const int c = threadIdx.x % TW, t = threadIdx.x / TW;
     const int P = a.nl / E;
-    const int col = blockIdx.x * TW + c;
-    C *base = a.spec + (long long)blockIdx.y * a.bs + col;
+    const int col = bx * TW + c;
+    C *base = a.spec + (long long)by * a.bs + col;
     C v[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = base[(long long)(t + P * q) * a.ls];
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 && E <= 8) ? 2 : 1) col_k
         const int hn = a.n0 / 2;
         const bool live = col <= a.n0 + hn;
         const T sx = live ? a.tx[col < a.n0 ? col : col - a.n0] : (T)0;
-        const T sb = a.tb ? a.tb[blockIdx.y] : (T)0;
+        const T sb = a.tb ? a.tb[by] : (T)0;
 #pragma unroll
         for (int q = 0; q < E; ++q) {
             const T sig = sx + a.tl[t + P * q] + sb;
@@ -169,6 +178,12 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 && E <= 8) ? 2 : 1) col_k
     if (MODE & 2) line_fft<E, +1, ColLayout>(v, sm + c, TW, a.nl, a.logn, t, P, a.tw);
 #pragma unroll
     for (int q = 0; q < E; ++q) base[(long long)(t + P * q) * a.ls] = v[q];
+}
+
+template <typename T, int E, int TW, int MODE>
+__global__ void __launch_bounds__(512, (sizeof(T) == 4 && E <= 8) ? 2 : 1) col_kernel(ColArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    col_body<T, E, TW, MODE>(a, blockIdx.x, blockIdx.y, smraw);
 }
 
 // ------------------------------------------------------------------ staged FP32 axis pass
@@ -254,18 +269,19 @@ static inline StagedPlan staged_plan(int nl) {
 
 // ------------------------------------------------------------------ x-pass inverse
 
+// Body of the inverse x-pass for row-pair group `bidx` (first `nthr` threads active).
 template <typename T, typename TIn, typename TOut, int E, int OUT>
-__global__ void __launch_bounds__(512) row_inv_kernel(RowArgs<T, TIn, TOut> a) {
+__device__ __forceinline__ void row_inv_body(const RowArgs<T, TIn, TOut> &a, long long bidx, int nthr, unsigned char *smraw) {
     using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smraw[];
     C *sm = reinterpret_cast<C *>(smraw);
+    const int tid = threadIdx.x;
     constexpr int LE = E >= 16 ? 4 : (E >= 8 ? 3 : (E >= 4 ? 2 : 1));
     const int n0 = a.n0, ln0 = a.logn0, P = n0 >> LE, lP = ln0 - LE, LS = RowLayout::size(n0), hn = n0 / 2;
-    const long long N = a.N, npairs = a.rows / 2, pair0 = (long long)blockIdx.x * a.G;
-    const int line = threadIdx.x >> lP, t = threadIdx.x & (P - 1);
+    const long long N = a.N, npairs = a.rows / 2, pair0 = bidx * a.G;
+    const int line = tid >> lP, t = tid & (P - 1);
     const int gp = line / 3, kind = line % 3;
     const long long pair = pair0 + gp;
-    const bool valid = pair < npairs;
+    const bool valid = gp < a.G && pair < npairs;
     C v[E];
     if (valid) {
         if (kind < 2) {
@@ -302,13 +318,13 @@ __global__ void __launch_bounds__(512) row_inv_kernel(RowArgs<T, TIn, TOut> a) {
     constexpr int XHI = (OUT == OUT_APPLY || OUT == OUT_MATVEC || OUT == OUT_JT) ? 4 : (OUT == OUT_FUSED ? 3 : 0);
     constexpr bool NEED_F = OUT == OUT_JT;
     const int total = 2 * a.G * n0;
-    for (int base = threadIdx.x; base < total; base += KC * blockDim.x) {
+    for (int base = tid; tid < nthr && base < total; base += KC * nthr) {
         T mv[KC][3];
         TIn xv[KC][4];
         T fv[KC][4];
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-            const int idx = base + k * blockDim.x;
+            const int idx = base + k * nthr;
             const int gq = idx >> (ln0 + 1), rr = (idx >> ln0) & 1, xx = idx & (n0 - 1);
             if (idx < total && pair0 + gq < npairs) {
                 const long long j = (2 * (pair0 + gq) + rr) * n0 + xx;
@@ -327,7 +343,7 @@ __global__ void __launch_bounds__(512) row_inv_kernel(RowArgs<T, TIn, TOut> a) {
         }
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-            const int idx = base + k * blockDim.x;
+            const int idx = base + k * nthr;
             const int gq = idx >> (ln0 + 1), rr = (idx >> ln0) & 1, xx = idx & (n0 - 1);
             if (!(idx < total && pair0 + gq < npairs)) continue;
             const long long j = (2 * (pair0 + gq) + rr) * n0 + xx;
@@ -378,6 +394,12 @@ __global__ void __launch_bounds__(512) row_inv_kernel(RowArgs<T, TIn, TOut> a) {
             }
         }
     }
+}
+
+template <typename T, typename TIn, typename TOut, int E, int OUT>
+__global__ void __launch_bounds__(512) row_inv_kernel(RowArgs<T, TIn, TOut> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    row_inv_body<T, TIn, TOut, E, OUT>(a, blockIdx.x, blockDim.x, smraw);
 }
 
 // elements per thread of a line: 8 (16 for 1024-point FP32 lines); FP64 stays at 8 so
