@@ -172,12 +172,18 @@ def main():
     ap.add_argument("--apply-sweep", default="", help="only time the isolated FFT-HSS apply on these grids, "
                     "e.g. '256^3,128^3,1024^2' (one JSON line each, with a per-pass breakdown)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --apply-sweep")
+    ap.add_argument("--ensemble", action="store_true", help="only the 96-problem batched ensemble (5 Euler steps)")
+    ap.add_argument("--adjoint", action="store_true", help="only the 512^2 adjoint timing (16 midpoint steps)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
     if args.apply_sweep:
         return apply_sweep(args)
+    if args.ensemble:
+        return ensemble_leg(args)
+    if args.adjoint:
+        return adjoint_leg(args)
 
     import numpy as np
     import torch
@@ -446,6 +452,121 @@ def apply_sweep(args):
         ctx.close()
         del m, p, z
         torch.cuda.empty_cache()
+
+
+def ensemble_leg(args):
+    """96 independent 2D problems (32 each of 128^2, 256^2, 512^2), alpha ~ U[0.01, 0.5],
+    dt = U[2, 16] x the explicit exchange limit, seeded smooth/broadband mixes, h = (0,0,0.5),
+    5 projected-Euler steps each with FP32-flexible GMRES(30) at rtol 1e-10: one persistent
+    launch (block count from the ensemble autotuner) vs the same problems one at a time
+    through the context API."""
+    import numpy as np
+    import torch
+    import paper_2607_15290_b300 as L
+    from paper_2607_15290_b300 import inputs as I
+    rng = np.random.default_rng(20260725)
+    steps = 5
+    specs = []
+    for n in (128, 256, 512):
+        for i in range(32):
+            alpha = float(rng.uniform(0.01, 0.5))
+            c = float(rng.uniform(2.0, 16.0))
+            w = float(rng.uniform(0.0, 1.0))
+            k = c * 2 * alpha / ((1 + alpha ** 2) * 2 * (np.pi * n) ** 2)
+            seed = 1000 * n + i
+            f = w * I.smooth2d((n, n), seed=seed) + (1 - w) * I.broadband((n, n), seed=seed)
+            f = f / np.sqrt((f * f).sum(0, keepdims=True))
+            specs.append((n, alpha, k, f))
+    opts = L.Opts(restart=30, rtol=1e-10, max_iters=900, precision=L.PREC_FP32_FLEX)
+    stream = torch.cuda.Stream()
+    probs = [{"n": (n, n), "params": L.Params(alpha=a, k=k, lam=0.5, h_ext=(0.0, 0.0, 0.5)),
+              "m": torch.tensor(f, device="cuda"), "x": torch.zeros((4, n, n), dtype=torch.float64, device="cuda")}
+             for n, a, k, f in specs]
+    m0 = [p["m"].clone() for p in probs]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ens = L.Ensemble(probs, opts, stream=stream)
+        blocks = ens.autotune()
+        for p, m in zip(probs, m0):
+            p["m"].copy_(m)
+        ens.run(1)                                   # warm-up (captures the graph for 1 step)
+        for p, m in zip(probs, m0):
+            p["m"].copy_(m)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos, used_graph = ens.run(steps)
+        e1.record(stream)
+    stream.synchronize()
+    ms_ens = e0.elapsed_time(e1)
+    # the same problems one at a time (one context per grid size, one Euler step per call)
+    ctxs = {n: L.Context((n, n)) for n in (128, 256, 512)}
+    for c in ctxs.values():
+        c.autotune(fp64=True, fp32=True)
+    seq = [m.clone() for m in m0]
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    iters_seq = 0
+    for idx, (n, a, k, f) in enumerate(specs):
+        prm = probs[idx]["params"]
+        m = seq[idx]
+        for _ in range(steps):
+            m, x, info = L.llg_step_euler(ctxs[n], prm, opts, m)
+            iters_seq += info["iters"]
+        seq[idx] = m
+    t1.record()
+    torch.cuda.synchronize()
+    ms_seq = t0.elapsed_time(t1)
+    diff = max(float((p["m"] - s_).abs().max()) for p, s_ in zip(probs, seq))
+    solves = len(specs) * steps
+    out = {"leg": "ensemble", "problems": len(specs), "steps": steps, "grids": "32 x 128^2, 32 x 256^2, 32 x 512^2",
+           "ensemble_ms": ms_ens, "ensemble_solves_per_s": solves / (ms_ens / 1e3),
+           "sequential_ms": ms_seq, "sequential_solves_per_s": solves / (ms_seq / 1e3),
+           "speedup_vs_one_at_a_time": ms_seq / ms_ens, "persistent_blocks": blocks, "cuda_graph": used_graph,
+           "max_abs_diff_vs_one_at_a_time": diff,
+           "iters_per_solve_ensemble": sum(i["iters"] for i in infos) / solves,
+           "iters_per_solve_sequential": iters_seq / solves,
+           "worst_rel_res": max(i["rel_res_true"] for i in infos),
+           "statuses": sorted(set(i["status"] for i in infos))}
+    print(json.dumps(out), flush=True)
+    ens.close()
+
+
+def adjoint_leg(args):
+    """Gradient of L = 1/2 |m(T) - m_target|^2 w.r.t. alpha, h and m0 through 16 midpoint steps on
+    512^2 at dt = 8x the explicit limit, checkpoint every 4 steps: forward time vs gradient time."""
+    import numpy as np
+    import torch
+    import paper_2607_15290_b300 as L
+    from paper_2607_15290_b300 import inputs as I
+    from paper_2607_15290_b300.autograd import midpoint_trajectory
+    n = (512, 512)
+    ctx = L.Context(n)
+    ctx.autotune(fp64=True, fp32=False)
+    alpha = 0.1
+    k = 8 * 2 * alpha / ((1 + alpha ** 2) * 2 * (np.pi * 512) ** 2)
+    m0 = torch.tensor(I.smooth2d(n, seed=41), device="cuda")
+    tgt = torch.tensor(I.smooth2d(n, seed=42, noise=0.2), device="cuda")
+    opts = L.Opts(rtol=1e-10, picard_tol=1e-10, restart=30)
+    res = {}
+    for rep in range(2):
+        a = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+        h = torch.tensor([0.0, 0.0, 0.5], dtype=torch.float64, requires_grad=True)
+        m = m0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mT = midpoint_trajectory(ctx, m, a, h, k, 16, opts=opts, checkpoint=4)
+        loss = 0.5 * ((mT - tgt) ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        res = {"forward_s": t1 - t0, "gradient_s": t2 - t1, "gradient_over_forward": (t2 - t1) / (t1 - t0),
+               "dL_dalpha": float(a.grad), "dL_dh": h.grad.tolist(), "loss": float(loss.detach())}
+    out = {"leg": "adjoint", "grid": list(n), "steps": 16, "checkpoint": 4, "dt_over_explicit_limit": 8.0,
+           "rtol": 1e-10, **res}
+    print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

@@ -127,6 +127,10 @@ struct EnsArgs {
     double *partials;          // [chunk][32]
     int *flags;                // [0]: any problem active, [1], [2]: any cycle still running (parity slots)
     EnsBarrier *bar;
+    const long long *rowoff;   // [nprob + 1] prefix sums of x-pass items
+    const long long *coloff;   // [nprob + 1] prefix sums of axis-pass items
+    unsigned *cnt;             // [nprob] chunk-arrival counters (last-block reductions)
+    double *partB, *partC;     // second and third partial-sum buffers ([chunk][32])
     long long nchunks;
     long long row_items[3], col_items[3];   // per class item counts
     int cls_of_group_offset;   // unused
@@ -152,47 +156,52 @@ template <typename T> __device__ __forceinline__ const T *sig_of(const EnsClass 
 template <> __device__ __forceinline__ const double *sig_of<double>(const EnsClass &C, int ax) { return C.sig64[ax]; }
 template <> __device__ __forceinline__ const float *sig_of<float>(const EnsClass &C, int ax) { return C.sig32[ax]; }
 
-// enumerate (problem, group) for an x-pass over all problems that are active
+// largest p with off[p] <= it (off has nprob + 1 entries, off[0] = 0)
+__device__ __forceinline__ int find_prob(const long long *off, int nprob, long long it) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// x-pass items: (problem, row-pair group), over all problems
 template <typename F>
 __device__ __forceinline__ void for_row_items(const EnsArgs &A, F f) {
-    long long total = 0;
-    for (int p = 0; p < A.nprob; ++p) {
-        const EnsClass &C = CL(A, p);
-        total += (A.prob[p].rows / 2 + C.G - 1) / C.G;
-    }
+    const long long total = A.rowoff[A.nprob];
     for (long long it = blockIdx.x; it < total; it += gridDim.x) {
-        long long rem = it;
-        int p = 0;
-        for (; p < A.nprob; ++p) {
-            const long long cnt = (A.prob[p].rows / 2 + CL(A, p).G - 1) / CL(A, p).G;
-            if (rem < cnt) break;
-            rem -= cnt;
-        }
-        f(p, rem);
+        const int p = find_prob(A.rowoff, A.nprob, it);
+        f(p, it - A.rowoff[p]);
     }
 }
 
+// axis-pass items: (problem, column tile)
 template <typename F>
 __device__ __forceinline__ void for_col_items(const EnsArgs &A, F f) {
-    long long total = 0;
-    for (int p = 0; p < A.nprob; ++p) total += CL(A, p).S / CL(A, p).TW;
+    const long long total = A.coloff[A.nprob];
     for (long long it = blockIdx.x; it < total; it += gridDim.x) {
-        long long rem = it;
-        int p = 0;
-        for (; p < A.nprob; ++p) {
-            const long long cnt = CL(A, p).S / CL(A, p).TW;
-            if (rem < cnt) break;
-            rem -= cnt;
-        }
-        f(p, (int)rem);
+        const int p = find_prob(A.coloff, A.nprob, it);
+        f(p, (int)(it - A.coloff[p]));
     }
+}
+
+// vector-chunk items: (problem, chunk); problems' chunks are consecutive from ch0
+__device__ __forceinline__ int find_chunk_prob(const EnsArgs &A, long long it) {
+    int lo = 0, hi = A.nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.prob[mid].ch0 <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 template <typename F>
 __device__ __forceinline__ void for_chunk_items(const EnsArgs &A, F f) {
     for (long long it = blockIdx.x; it < A.nchunks; it += gridDim.x) {
-        int p = 0;
-        while (p + 1 < A.nprob && A.prob[p + 1].ch0 <= it) ++p;
+        const int p = find_chunk_prob(A, it);
         f(p, (int)(it - A.prob[p].ch0));
     }
 }
@@ -255,9 +264,40 @@ __device__ __forceinline__ void store_partials(const EnsArgs &A, const EnsProb &
     block_reduce_store<ENS_MAXM>(acc, nv, A.partials + (P.ch0 + ch) * 32);
 }
 
+// After a block has stored its chunk partials in buf: count the arrival; returns true (for
+// the whole block) in the block that completes problem p's count, which then owns the
+// final reduction; the counter is reset for the next pass.
+__device__ __forceinline__ bool last_chunk(const EnsArgs &A, int p) {
+    __shared__ int s_last;
+    __threadfence();   // every thread's partials are visible device-wide before the count
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned c = atomicAdd(&A.cnt[p], 1u) + 1u;
+        s_last = c == (unsigned)A.prob[p].nch;
+        if (s_last) {
+            A.cnt[p] = 0u;
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+// sum over the chunks of problem p of buf[chunk][i], i < cnt, read through L2
+__device__ __forceinline__ void sum_chunks_buf(const EnsProb &P, const double *buf, int cnt, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < cnt; i += ENS_THREADS / 32) {
+        double s = 0.0;
+        for (int c = lane; c < P.nch; c += 32) s += __ldcg(&buf[(P.ch0 + c) * 32 + i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) out[i] = s;
+    }
+}
+
 // ---------------------------------------------------------------- the persistent kernel
 
-__global__ void __launch_bounds__(ENS_THREADS) ens_kernel(EnsArgs A) {
+__global__ void __launch_bounds__(ENS_THREADS, 2) ens_kernel(EnsArgs A) {
     extern __shared__ __align__(16) unsigned char smraw[];
     EnsState *S = A.st;
     const int tid = threadIdx.x;
@@ -401,8 +441,10 @@ __global__ void __launch_bounds__(ENS_THREADS) ens_kernel(EnsArgs A) {
                     __syncthreads();
                 });
                 if (!bar_sync(A.bar, __LINE__)) return;
-                // CGS2 in FP64: h1 = V^T w
+                // CGS2 in FP64, three passes; the block that completes a problem's chunks
+                // performs that problem's reduction (no separate reduce phases)
                 const int nv = j + 1;
+                // pass A: h1 = V^T w
                 for_chunk_items(A, [&](int p, int ch) {
                     const EnsProb &P = A.prob[p];
                     if (S[p].cyc_done) return;
@@ -413,27 +455,21 @@ __global__ void __launch_bounds__(ENS_THREADS) ens_kernel(EnsArgs A) {
                     for (int i = 0; i < ENS_MAXM; ++i) acc[i] = 0.0;
                     for (long long e = lo + tid; e < hi; e += ENS_THREADS) {
                         const double w = P.W[e];
-                        double vv[ENS_MAXM];
-#pragma unroll
-                        for (int i = 0; i < ENS_MAXM; ++i) vv[i] = i < nv ? P.V[(long long)i * P.n4 + e] : 0.0;
 #pragma unroll
                         for (int i = 0; i < ENS_MAXM; ++i)
-                            if (i < nv) acc[i] += vv[i] * w;
+                            if (i < nv) acc[i] += __ldcs(&P.V[(long long)i * P.n4 + e]) * w;
                     }
-                    store_partials(A, P, ch, acc, nv);
+                    block_reduce_store<ENS_MAXM>(acc, nv, A.partials + (P.ch0 + ch) * 32);
+                    if (last_chunk(A, p)) {
+                        __shared__ double tot1[ENS_MAXM];
+                        sum_chunks_buf(P, A.partials, nv, tot1);
+                        __syncthreads();
+                        if (tid < nv) S[p].h1[tid] = tot1[tid] * S[p].scale[tid];
+                    }
                     __syncthreads();
                 });
                 if (!bar_sync(A.bar, __LINE__)) return;
-                for (int p = blockIdx.x; p < A.nprob; p += gridDim.x) {
-                    if (S[p].cyc_done) continue;
-                    __shared__ double tot1[ENS_MAXM];
-                    sum_chunks(A, A.prob[p], nv, tot1);
-                    __syncthreads();
-                    if (tid < nv) S[p].h1[tid] = tot1[tid] * S[p].scale[tid];
-                    __syncthreads();
-                }
-                if (!bar_sync(A.bar, __LINE__)) return;
-                // w <- w - V h1 ; h2 = V^T w
+                // pass B: w <- w - V h1 ; h2 = V^T w
                 for_chunk_items(A, [&](int p, int ch) {
                     const EnsProb &P = A.prob[p];
                     if (S[p].cyc_done) return;
@@ -455,20 +491,18 @@ __global__ void __launch_bounds__(ENS_THREADS) ens_kernel(EnsArgs A) {
                         for (int i = 0; i < ENS_MAXM; ++i)
                             if (i < nv) acc[i] += P.V[(long long)i * P.n4 + e] * w;
                     }
-                    store_partials(A, P, ch, acc, nv);
+                    block_reduce_store<ENS_MAXM>(acc, nv, A.partB + (P.ch0 + ch) * 32);
+                    if (last_chunk(A, p)) {
+                        __shared__ double tot2[ENS_MAXM];
+                        sum_chunks_buf(P, A.partB, nv, tot2);
+                        __syncthreads();
+                        if (tid < nv) S[p].h2[tid] = tot2[tid] * S[p].scale[tid];
+                    }
                     __syncthreads();
                 });
                 if (!bar_sync(A.bar, __LINE__)) return;
-                for (int p = blockIdx.x; p < A.nprob; p += gridDim.x) {
-                    if (S[p].cyc_done) continue;
-                    __shared__ double tot2[ENS_MAXM];
-                    sum_chunks(A, A.prob[p], nv, tot2);
-                    __syncthreads();
-                    if (tid < nv) S[p].h2[tid] = tot2[tid] * S[p].scale[tid];
-                    __syncthreads();
-                }
-                if (!bar_sync(A.bar, __LINE__)) return;
-                // V_{j+1} = w - V h2 (unnormalised), ||V_{j+1}||^2
+                // pass C: V_{j+1} = w - V h2 (unnormalised), ||V_{j+1}||^2, then the Hessenberg
+                // column, Givens rotation and stopping test by the completing block
                 for_chunk_items(A, [&](int p, int ch) {
                     const EnsProb &P = A.prob[p];
                     if (S[p].cyc_done) return;
@@ -488,50 +522,46 @@ __global__ void __launch_bounds__(ENS_THREADS) ens_kernel(EnsArgs A) {
                         vn[e] = w;
                         acc[0] += w * w;
                     }
-                    store_partials(A, P, ch, acc, 1);
-                    __syncthreads();
-                });
-                if (!bar_sync(A.bar, __LINE__)) return;
-                // Hessenberg column, Givens rotation, stopping test
-                for (int p = blockIdx.x; p < A.nprob; p += gridDim.x) {
-                    if (S[p].cyc_done) continue;
-                    __shared__ double tot3[ENS_MAXM];
-                    sum_chunks(A, A.prob[p], 1, tot3);
-                    __syncthreads();
-                    if (tid == 0) {
-                        EnsState &s = S[p];
-                        const int ld = ENS_MAXM + 1;
-                        double *H = s.H;
-                        for (int i = 0; i <= j; ++i) H[i + ld * j] = s.h1[i] + s.h2[i];
-                        const double hn = sqrt(tot3[0]);
-                        H[j + 1 + ld * j] = hn;
-                        s.scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-                        for (int i = 0; i < j; ++i) {
-                            const double a = H[i + ld * j], b = H[i + 1 + ld * j];
-                            H[i + ld * j] = s.cs[i] * a + s.sn[i] * b;
-                            H[i + 1 + ld * j] = -s.sn[i] * a + s.cs[i] * b;
+                    block_reduce_store<ENS_MAXM>(acc, 1, A.partC + (P.ch0 + ch) * 32);
+                    if (last_chunk(A, p)) {
+                        __shared__ double tot3[ENS_MAXM];
+                        sum_chunks_buf(P, A.partC, 1, tot3);
+                        __syncthreads();
+                        if (tid == 0) {
+                            EnsState &s = S[p];
+                            const int ld = ENS_MAXM + 1;
+                            double *H = s.H;
+                            for (int i = 0; i <= j; ++i) H[i + ld * j] = s.h1[i] + s.h2[i];
+                            const double hn = sqrt(tot3[0]);
+                            H[j + 1 + ld * j] = hn;
+                            s.scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+                            for (int i = 0; i < j; ++i) {
+                                const double a = H[i + ld * j], b = H[i + 1 + ld * j];
+                                H[i + ld * j] = s.cs[i] * a + s.sn[i] * b;
+                                H[i + 1 + ld * j] = -s.sn[i] * a + s.cs[i] * b;
+                            }
+                            const double a = H[j + ld * j], b = H[j + 1 + ld * j], rr = hypot(a, b);
+                            const double cs = rr > 0.0 ? a / rr : 1.0, sn = rr > 0.0 ? b / rr : 0.0;
+                            s.cs[j] = cs;
+                            s.sn[j] = sn;
+                            H[j + ld * j] = rr;
+                            H[j + 1 + ld * j] = 0.0;
+                            s.g[j + 1] = -sn * s.g[j];
+                            s.g[j] = cs * s.g[j];
+                            s.jd = j + 1;
+                            s.iters++;
+                            const double est = fabs(s.g[j + 1]);
+                            if (!isfinite(est)) {
+                                s.status = LLG_ERR_BREAKDOWN;
+                                s.cyc_done = 1;
+                            } else if (est <= s.target || hn == 0.0 || j + 1 == A.m || s.iters >= A.max_iters) {
+                                s.cyc_done = 1;
+                            }
+                            if (!s.cyc_done) atomicOr(cyc_flag, 1);
                         }
-                        const double a = H[j + ld * j], b = H[j + 1 + ld * j], rr = hypot(a, b);
-                        const double cs = rr > 0.0 ? a / rr : 1.0, sn = rr > 0.0 ? b / rr : 0.0;
-                        s.cs[j] = cs;
-                        s.sn[j] = sn;
-                        H[j + ld * j] = rr;
-                        H[j + 1 + ld * j] = 0.0;
-                        s.g[j + 1] = -sn * s.g[j];
-                        s.g[j] = cs * s.g[j];
-                        s.jd = j + 1;
-                        s.iters++;
-                        const double est = fabs(s.g[j + 1]);
-                        if (!isfinite(est)) {
-                            s.status = LLG_ERR_BREAKDOWN;
-                            s.cyc_done = 1;
-                        } else if (est <= s.target || hn == 0.0 || j + 1 == A.m || s.iters >= A.max_iters) {
-                            s.cyc_done = 1;
-                        }
-                        if (!s.cyc_done) atomicOr(cyc_flag, 1);
                     }
                     __syncthreads();
-                }
+                });
                 if (!bar_sync(A.bar, __LINE__)) return;
                 if (*(volatile int *)cyc_flag == 0) break;
             }
@@ -688,6 +718,9 @@ struct llg_ensemble {
     double *partials = nullptr;
     int *flags = nullptr;
     EnsBarrier *bar = nullptr;
+    long long *rowoff = nullptr, *coloff = nullptr;
+    unsigned *cnt = nullptr;
+    double *partB = nullptr, *partC = nullptr;
     long long nchunks = 0;
     EnsState *hst = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -848,12 +881,28 @@ llg_status llg_ensemble_create(const llg_problem *probs, int count, const llg_op
         ens_alloc(e, &e->dst, sizeof(EnsState) * count) != cudaSuccess ||
         ens_alloc(e, &e->partials, sizeof(double) * 32 * (size_t)ch) != cudaSuccess ||
         ens_alloc(e, &e->flags, sizeof(int) * 4) != cudaSuccess ||
-        ens_alloc(e, &e->bar, sizeof(EnsBarrier)) != cudaSuccess)
+        ens_alloc(e, &e->bar, sizeof(EnsBarrier)) != cudaSuccess ||
+        ens_alloc(e, &e->rowoff, sizeof(long long) * (count + 1)) != cudaSuccess ||
+        ens_alloc(e, &e->coloff, sizeof(long long) * (count + 1)) != cudaSuccess ||
+        ens_alloc(e, &e->cnt, sizeof(unsigned) * count) != cudaSuccess ||
+        ens_alloc(e, &e->partB, sizeof(double) * 32 * (size_t)ch) != cudaSuccess ||
+        ens_alloc(e, &e->partC, sizeof(double) * 32 * (size_t)ch) != cudaSuccess)
         return fail(LLG_ERR_OOM, "descriptors");
     if (cudaMallocHost(&e->hst, sizeof(EnsState) * count) != cudaSuccess) return fail(LLG_ERR_OOM, "host state");
     cudaMemcpy(e->dcls, e->cls.data(), sizeof(EnsClass) * e->cls.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(e->dprob, e->prob.data(), sizeof(EnsProb) * count, cudaMemcpyHostToDevice);
     cudaMemset(e->dst, 0, sizeof(EnsState) * count);
+    cudaMemset(e->cnt, 0, sizeof(unsigned) * count);
+    {
+        std::vector<long long> ro(count + 1, 0), co(count + 1, 0);
+        for (int q = 0; q < count; ++q) {
+            const EnsClass &C = e->cls[e->prob[q].cls];
+            ro[q + 1] = ro[q] + (e->prob[q].rows / 2 + C.G - 1) / C.G;
+            co[q + 1] = co[q] + C.S / C.TW;
+        }
+        cudaMemcpy(e->rowoff, ro.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice);
+        cudaMemcpy(e->coloff, co.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice);
+    }
     // co-resident blocks for the cooperative launch
     cudaError_t r = cudaFuncSetAttribute(ens_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ENS_SMEM);
     int per_sm = 0, dev = 0, sms = 0;
@@ -959,6 +1008,11 @@ llg_status llg_ensemble_run(llg_ensemble *e, int steps, llg_info *infos, int *us
     A.partials = e->partials;
     A.flags = e->flags;
     A.bar = e->bar;
+    A.rowoff = e->rowoff;
+    A.coloff = e->coloff;
+    A.cnt = e->cnt;
+    A.partB = e->partB;
+    A.partC = e->partC;
     A.nchunks = e->nchunks;
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
