@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <algorithm>
 #include "spectral_kernels.cuh"
+#include "spectral_ct_launch.h"
 
 namespace llg {
 
@@ -156,10 +157,14 @@ template <typename T> static ColCfg col_default(int nl) {
 template <typename T>
 static cudaError_t launch_col_cfg(llg_ctx *c, int mode, const ColArgs<T> &a, int batches, const ColCfg &cfg) {
     if (cfg.kind == 1) {
-        if constexpr (sizeof(T) == 4) return launch_staged(c, mode, a, a.n0 + a.n0 / 2 + 1, batches, cfg.TW, cfg.CB);
+        if constexpr (sizeof(T) == 4) {
+            if (ct::covers(a.logn)) return ct::staged(c, a.logn, mode, a, a.n0 + a.n0 / 2 + 1, batches, cfg.TW, cfg.CB);
+            return launch_staged(c, mode, a, a.n0 + a.n0 / 2 + 1, batches, cfg.TW, cfg.CB);
+        }
         return cudaErrorInvalidValue;
     }
     const dim3 grid(a.S / cfg.TW, batches);
+    if (ct::covers(a.logn) && cfg.E == col_E<T>(a.nl)) return ct::col<T>(c, a.logn, mode, a, grid, cfg.TW);
 #define LLG_CE(EE, TT) if (cfg.E == EE && cfg.TW == TT) return launch_col_ETW<T, EE, TT>(c, mode, a, grid);
     if constexpr (sizeof(T) == 8) {
         LLG_CE(2, 8) LLG_CE(4, 8) LLG_CE(8, 8) LLG_CE(2, 4) LLG_CE(4, 4) LLG_CE(8, 4)
@@ -213,7 +218,8 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
     if (want < G) G = (int)(want < 1 ? 1 : want);
     const int blocks = (int)((pairs + G - 1) / G);
     const int threads = 3 * G * P;
-    const size_t smr = (size_t)3 * G * RowLayout::size(n0) * sizeof(cplx<T>);
+    const bool rct = ct::covers(g.logn[0]);
+    const size_t smr = rct ? ct::row_smem<T>(n0, G) : (size_t)3 * G * RowLayout::size(n0) * sizeof(cplx<T>);
 
     RowArgs<T, TIn, TOut> ra;
     ra.spec = spec_of<T>(c);
@@ -251,7 +257,8 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
             break;                                                                            \
     }
     prof_begin(c, K_XFWD, in_b + live * CB, xf);
-    LLG_DISPATCH_E(launch_row_fwd_E, in_mode)
+    if (rct) e = ct::row_fwd<T, TIn, TOut>(c, g.logn[0], in_mode, ra, blocks, threads, smr);
+    else { LLG_DISPATCH_E(launch_row_fwd_E, in_mode) }
     prof_end(c);
     if (e != cudaSuccess) return cuda_check(c, e, "x-pass forward");
     c->launches++;
@@ -277,7 +284,8 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
         if ((e = run_slot(SLOT_Y_INV, fftf(ylines, g.n[1], g.logn[1]))) != cudaSuccess) return cuda_check(c, e, "y-pass inverse");
     }
     prof_begin(c, K_XINV, live * CB + out_b, xf);
-    LLG_DISPATCH_E(launch_row_inv_E, out_mode)
+    if (rct) e = ct::row_inv<T, TIn, TOut>(c, g.logn[0], out_mode, ra, blocks, threads, smr);
+    else { LLG_DISPATCH_E(launch_row_inv_E, out_mode) }
     prof_end(c);
 #undef LLG_DISPATCH_E
     if (e != cudaSuccess) return cuda_check(c, e, "x-pass inverse");

@@ -55,13 +55,24 @@ def central_difference(mp, mm, tgt, eps):
     return float(((mp - mm) * (0.5 * (mp + mm) - tgt)).sum()) / (2 * eps)
 
 
-def test_adjoint_gradient_matches_oracle():
-    n = (32, 16)
+@pytest.mark.parametrize("n,k", [((32, 16), 2e-3), ((64, 128), 2e-5)])
+def test_adjoint_gradient_matches_oracle(n, k):
+    """(32, 16) runs the generic-length kernels, (64, 128) the compile-time-length ones
+    (the oracle uses its radix-2 FFT there, pinned against the naive DFT)."""
+    if n[0] >= 64:
+        O.set_transform(O.FFT)
+    try:
+        _adjoint_vs_oracle(n, k)
+    finally:
+        O.set_transform(O.DFT)
+
+
+def _adjoint_vs_oracle(n, k):
     og = O.Grid(n)
     ctx = L.Context(n)
     m0 = I.smooth2d(n, seed=31, noise=0.05)
     tgt = I.smooth2d(n, seed=32, noise=0.3)
-    alpha, h, k, nsteps = 0.1, (0.1, -0.2, 0.5), 2e-3, 5
+    alpha, h, nsteps = 0.1, (0.1, -0.2, 0.5), 5
     opts = L.Opts(rtol=1e-13, picard_tol=1e-13, restart=30)
     loss, da, dh, dm0 = loss_and_grads(ctx, torch.tensor(m0, device="cuda"), torch.tensor(tgt, device="cuda"),
                                        alpha, h, k, nsteps, opts, checkpoint=2)

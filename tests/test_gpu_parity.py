@@ -247,3 +247,38 @@ def test_autotuned_shapes_keep_parity(dev, n):
     assert rel(got32, ref) <= 2e-5
     ref_t = O.saddle_apply(og, po, m, p, transpose=True)
     assert rel(host(L.llg_saddle_apply(ctx, pl, gpu(m), gpu(p), transpose=True)), ref_t) <= 1e-12
+
+
+# Grids whose axes cover every line length with a compile-time plan (64..1024) in each
+# role: x rows (nodal prologue/epilogue), y columns and z columns (forward, multiplier,
+# inverse), in FP64 and FP32, before and after the autotuner picks staged shapes.
+CT_GRIDS = [(128, 512, 16), (16, 8, 512), (8, 16, 1024), (256, 8, 256), (512, 256), (1024, 64), (64, 128)]
+
+
+@pytest.fixture
+def oracle_fft():
+    O.set_transform(O.FFT)   # the textbook radix-2 FFT, pinned against the naive DFT
+    yield
+    O.set_transform(O.DFT)
+
+
+@pytest.mark.parametrize("n", CT_GRIDS, ids=[str(g) for g in CT_GRIDS])
+def test_compiled_lengths_parity(dev, oracle_fft, n):
+    og = O.Grid(n)
+    ctx = L.Context(n)
+    m = I.random_unit(n, seed=114) * 1.05
+    p = I.random_saddle_vector(n, seed=115)
+    po, pl = prm_pair(alpha=0.1, k=2e-4, theta=0.5)
+    gm, gp, gm32, gp32 = gpu(m), gpu(p), gpu(m, torch.float32), gpu(p, torch.float32)
+    for tuned in (False, True):
+        if tuned:
+            assert "->" in ctx.autotune()
+        for transpose in (False, True):
+            ref = O.ffthss_apply(og, po, m, p, transpose=transpose)
+            assert rel(host(L.llg_ffthss_apply(ctx, pl, gm, gp, transpose=transpose)), ref) <= 1e-12, (tuned, transpose)
+            got32 = host(L.llg_ffthss_apply_f32(ctx, pl, gm32, gp32, transpose=transpose))
+            assert rel(got32, ref) <= 2e-5, (tuned, transpose)
+            ref_s = O.saddle_apply(og, po, m, p, transpose=transpose)
+            assert rel(host(L.llg_saddle_apply(ctx, pl, gm, gp, transpose=transpose)), ref_s) <= 1e-12, (tuned, transpose)
+        ref_f = O.ffthss_apply(og, po, m, O.saddle_apply(og, po, m, p))
+        assert rel(host(L.llg_precond_saddle_apply(ctx, pl, gm, gp)), ref_f) <= 1e-12, tuned
