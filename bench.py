@@ -172,8 +172,12 @@ def main():
     ap.add_argument("--apply-sweep", default="", help="only time the isolated FFT-HSS apply on these grids, "
                     "e.g. '256^3,128^3,1024^2' (one JSON line each, with a per-pass breakdown)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --apply-sweep")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="--apply-sweep with the default launch shapes (for profiling the passes alone)")
     ap.add_argument("--ensemble", action="store_true", help="only the 96-problem batched ensemble (5 Euler steps)")
     ap.add_argument("--adjoint", action="store_true", help="only the 512^2 adjoint timing (16 midpoint steps)")
+    ap.add_argument("--n", type=int, default=128,
+                    help="grid points per axis of the midpoint workload (128; smaller only for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -199,7 +203,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = workload_params()
+    w = workload_params(args.n)
     n = w["n"]
     N = n[0] * n[1] * n[2]
     ctx = L.Context(n)
@@ -309,6 +313,53 @@ def main():
         dist.destroy_process_group()
 
 
+def cufft_apply_compare(L, I, ctx, prm, nn, ours_ms):
+    """Comparison point: the same FP32 FFT-HSS apply with cuFFT (torch.fft R2C/C2R over the
+    three velocity components) for Algorithm 1's transforms and PyTorch elementwise kernels
+    for the symbol division and the closed-form nodal inverse (unfused).  Checked against
+    the library's apply on the same inputs, then timed with CUDA events."""
+    import numpy as np
+    import torch
+    nx, ny, nz = nn
+    N = nx * ny * nz
+    two_pi = 2.0 * np.pi
+    fz = torch.fft.fftfreq(nz, d=1.0 / nz, device="cuda", dtype=torch.float64) * two_pi
+    fy = torch.fft.fftfreq(ny, d=1.0 / ny, device="cuda", dtype=torch.float64) * two_pi
+    fx = torch.fft.rfftfreq(nx, d=1.0 / nx, device="cuda", dtype=torch.float64) * two_pi
+    sigma = fz[:, None, None] ** 2 + fy[None, :, None] ** 2 + fx[None, None, :] ** 2
+    chat = (1.0 + prm.alpha ** 2) * prm.c_ex
+    inv = (1.0 / (prm.alpha + prm.theta * prm.k * chat * sigma + prm.lam)).to(torch.float32)
+    lam = float(prm.lam)
+    m = torch.tensor(I.smooth3d(nn), device="cuda").float()
+    p = torch.randn((4, nz, ny, nx), device="cuda", dtype=torch.float32)
+
+    def apply():
+        w = torch.fft.irfftn(torch.fft.rfftn(p[:3], dim=(1, 2, 3)) * inv, s=(nz, ny, nx), dim=(1, 2, 3))
+        q4 = p[3] / lam
+        d = 1.0 / (lam * lam + (m * m).sum(0))
+        z = torch.empty_like(p)
+        z[:3] = (lam * w - torch.linalg.cross(m, w, dim=0) - m * q4) * d
+        z[3] = (lam * q4 + (m * w).sum(0)) * d
+        return z
+
+    ref = L.llg_ffthss_apply_f32(ctx, prm, m, p)
+    torch.cuda.synchronize()
+    diff = float((apply() - ref).abs().max() / ref.abs().max())
+    for _ in range(3):
+        apply()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        apply()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"ms": ms, "applies_per_s": 1e3 / ms, "ours_ms": ours_ms, "ours_speedup": ms / ours_ms,
+            "max_rel_diff_vs_ours": diff, "what": "torch.fft (cuFFT) R2C/C2R + unfused PyTorch elementwise nodal inverse"}
+
+
 def extras_leg(L, I, ctx, prm, w, m0, args):
     """FP32-flexible vs all-FP64 solve of one identical system, the isolated apply sweep and
     the end-to-end (host buffer) figure.  Runs after the timed region."""
@@ -373,6 +424,8 @@ def extras_leg(L, I, ctx, prm, w, m0, args):
     ex["apply_fp32_128"] = apply_rate(ctx, n)
     c256 = L.Context((256, 256, 256))
     ex["apply_fp32_256"] = apply_rate(c256, (256, 256, 256))
+    ex["cufft_apply_fp32"] = {"128": cufft_apply_compare(L, I, ctx, prm, n, ex["apply_fp32_128"]["ms"]),
+                              "256": cufft_apply_compare(L, I, c256, prm, (256, 256, 256), ex["apply_fp32_256"]["ms"])}
     c256.close()
     torch.cuda.empty_cache()
 
@@ -415,7 +468,7 @@ def apply_sweep(args):
         n = (int(base),) * int(dim)
         N = int(np.prod(n))
         ctx = L.Context(n)
-        tuning = ctx.autotune(fp64=args.precision == "fp64", fp32=args.precision == "fp32")
+        tuning = "" if args.no_autotune else ctx.autotune(fp64=args.precision == "fp64", fp32=args.precision == "fp32")
         f32 = args.precision == "fp32"
         dt = torch.float32 if f32 else torch.float64
         m = torch.tensor(I.smooth3d(n) if len(n) == 3 else I.smooth2d(n), device="cuda").to(dt)

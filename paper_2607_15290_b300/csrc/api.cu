@@ -478,7 +478,7 @@ llg_status llg_create(const llg_grid *grid, void *cuda_stream, llg_ctx **out) {
             cudaMemcpy(c->sig32[ex][l], s32[ex].data(), sizeof(float) * n, cudaMemcpyHostToDevice);
         }
     }
-    if ((e = cudaMalloc(&c->red, sizeof(double) * RB_STRIDE * reduction_blocks(c))) != cudaSuccess) return fail(e, "scratch");
+    if ((e = cudaMalloc(&c->red, sizeof(double) * RB_STRIDE * partial_capacity(c))) != cudaSuccess) return fail(e, "scratch");
     if ((e = cudaMalloc(&c->dsc, sizeof(double) * 64)) != cudaSuccess) return fail(e, "scratch");
     if ((e = cudaMallocHost(&c->hsc, sizeof(double) * 64)) != cudaSuccess) return fail(e, "pinned scratch");
     if ((e = cudaMalloc(&c->gdev, sizeof(GmresDev))) != cudaSuccess) return fail(e, "GMRES state");

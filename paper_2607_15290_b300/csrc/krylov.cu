@@ -5,8 +5,9 @@
 // over the basis: (A) h1 = V^T w; (B) w <- w - V h1 fused with h2 = V^T w;
 // (C) w <- w - V h2 fused with ||w||^2, written straight into V_{j+1}.  Basis
 // vectors are stored unnormalised with a device-side scale factor, so no extra
-// normalisation pass is needed.  Dot products reduce per block and then in one
-// block in a fixed order (deterministic).  The Hessenberg column, Givens
+// normalisation pass is needed.  Dot products reduce per block; the block that
+// finishes a pass last sums the partials in a fixed order (deterministic) and
+// updates the Arnoldi state, so a step is three launches.  The Hessenberg column, Givens
 // rotations, residual estimate and stopping flag live on the device; kernels of
 // later iterations return immediately once the flag is set, so the host only
 // synchronises every few iterations and once per cycle.
@@ -19,15 +20,72 @@
 namespace llg {
 
 int reduction_blocks(llg_ctx *c) { return 2 * c->sm_count; }
+int partial_capacity(llg_ctx *c) { return 8 * c->sm_count; }
 
 // ------------------------------------------------------------------ Arnoldi passes
 
 enum { PASS_DOT = 0, PASS_UPD_DOT = 1, PASS_UPD_NRM = 2 };
 
+// Finish of Arnoldi pass `mode` of step j, run by the block that completes the pass
+// last: sums the per-block partials in a fixed order, then
+//   mode 0: h1 = scale .* sums;  mode 1: h2 = scale .* sums;
+//   mode 2: ||w||^2 -> Hessenberg column h1 + h2 and h_{j+1,j}, previous Givens
+//           rotations applied, new rotation, residual estimate, stopping flag.
+// The state the sequential part needs is first gathered into shared memory by all
+// threads, so the single-thread part runs on shared memory, not on a chain of
+// dependent global loads.
+__device__ __noinline__ void arnoldi_finish(const double *partials, int nb, int nv, GmresDev *gd, int mode, int j) {
+    __shared__ double tot[64];
+    __shared__ double col[GmresDev::LD + 1], cs_s[GmresDev::MAXM], sn_s[GmresDev::MAXM];
+    __shared__ double gj;
+    block_sum_partials_l2(partials, nb, mode == PASS_UPD_NRM ? 1 : nv, tot);
+    __syncthreads();
+    if (mode != PASS_UPD_NRM) {
+        double *h = mode == PASS_DOT ? gd->h1 : gd->h2;
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) h[i] = tot[i] * gd->scale[i];
+        return;
+    }
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = gd->h1[i] + gd->h2[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        cs_s[i] = gd->cs[i];
+        sn_s[i] = gd->sn[i];
+    }
+    if (threadIdx.x == 0) gj = gd->g[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double hn = sqrt(tot[0]);
+        col[j + 1] = hn;
+        for (int i = 0; i < j; ++i) {
+            const double a = col[i], b = col[i + 1];
+            col[i] = cs_s[i] * a + sn_s[i] * b;
+            col[i + 1] = -sn_s[i] * a + cs_s[i] * b;
+        }
+        const double a = col[j], b = col[j + 1];
+        const double rr = hypot(a, b);
+        const double cs = rr > 0.0 ? a / rr : 1.0, sn = rr > 0.0 ? b / rr : 0.0;
+        col[j] = rr;
+        col[j + 1] = 0.0;
+        gd->cs[j] = cs;
+        gd->sn[j] = sn;
+        gd->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+        gd->g[j + 1] = -sn * gj;
+        gd->g[j] = cs * gj;
+        gd->jd = j + 1;
+        const double est = fabs(sn * gj);
+        if (!isfinite(est) || !isfinite(hn)) {
+            gd->breakdown = 1;
+            gd->done = 1;
+        } else if (est <= gd->target || hn == 0.0) {
+            gd->done = 1;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) gd->H[i + GmresDev::LD * j] = col[i];
+}
+
 template <int MAXV, int MODE>
 __global__ void __launch_bounds__(RB_THREADS) arnoldi_pass(const double *__restrict__ V, long long ldv, int nv,
-                                                                const GmresDev *__restrict__ gd,
-                                                                const double *win, double *wout, long long n,
+                                                                GmresDev *gd, const double *win, double *wout, long long n,
                                                                 double *__restrict__ partials) {
     if (gd->done) return;
     __shared__ double coef[MAXV];
@@ -69,54 +127,62 @@ __global__ void __launch_bounds__(RB_THREADS) arnoldi_pass(const double *__restr
             }
         }
     }
-    block_reduce_store<MAXV>(acc, MODE == PASS_UPD_NRM ? 1 : nv, partials + (long long)blockIdx.x * 64);
+    block_reduce_store<MAXV>(acc, MODE == PASS_UPD_NRM ? 1 : nv, partials + (long long)blockIdx.x * RB_STRIDE);
+    if (last_block_arrived(&gd->arrived)) arnoldi_finish(partials, gridDim.x, nv, gd, MODE, nv - 1);
 }
 
-// Sum the per-block partials (fixed order) and finish the Arnoldi step.
-// MODE 0: h1 = scale .* sums; MODE 1: h2 = scale .* sums; MODE 2: ||w||^2 -> Givens update.
-__global__ void __launch_bounds__(RB_THREADS) arnoldi_reduce(const double *__restrict__ partials, int nb, int nv,
-                                                             GmresDev *gd, int mode, int j) {
+// Passes A and C (one multiply-add per loaded basis value) for up to 16 basis
+// vectors, software-pipelined: the basis values of the thread's next element are
+// loaded before the multiply-adds of the current one, so memory latency overlaps
+// the FP64 pipe instead of alternating with it (pass B has twice the arithmetic per
+// load and saturates the pipe without this).
+template <int MAXV, int MODE>
+__global__ void __launch_bounds__(RB_THREADS, MAXV <= 8 ? 2 : 1) arnoldi_pass_pipe(const double *__restrict__ V, long long ldv, int nv,
+                                                                                     GmresDev *gd, const double *win, double *wout,
+                                                                                     long long n, double *__restrict__ partials) {
+    static_assert(MODE == PASS_DOT || MODE == PASS_UPD_NRM, "pipelined form covers passes A and C");
     if (gd->done) return;
-    __shared__ double tot[64];
-    block_sum_partials(partials, nb, mode == 2 ? 1 : nv, tot);
+    __shared__ double coef[MAXV];
+    if (threadIdx.x < nv) coef[threadIdx.x] = MODE == PASS_UPD_NRM ? gd->h2[threadIdx.x] * gd->scale[threadIdx.x] : 0.0;
     __syncthreads();
-    if (mode == 0) {
-        for (int i = threadIdx.x; i < nv; i += blockDim.x) gd->h1[i] = tot[i] * gd->scale[i];
-        return;
+    double acc[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) acc[i] = 0.0;
+    long long lo, hi;
+    block_chunk(n, lo, hi);
+    const long long bd = blockDim.x;
+    double va[MAXV], vb[MAXV], wa = 0.0, wb = 0.0;
+    auto load = [&](double (&vv)[MAXV], double &w, long long e) {
+        if (e < hi) {
+            w = win[e];
+#pragma unroll
+            for (int i = 0; i < MAXV; ++i) vv[i] = (i < nv) ? __ldg(&V[i * ldv + e]) : 0.0;
+        }
+    };
+    auto work = [&](const double (&vv)[MAXV], double w, long long e) {
+        if (e >= hi) return;
+        if (MODE == PASS_DOT) {
+#pragma unroll
+            for (int i = 0; i < MAXV; ++i)
+                if (i < nv) acc[i] += vv[i] * w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < MAXV; ++i)
+                if (i < nv) w -= coef[i] * vv[i];
+            wout[e] = w;
+            acc[0] += w * w;
+        }
+    };
+    long long e = lo + threadIdx.x;
+    load(va, wa, e);
+    for (; e < hi; e += 2 * bd) {
+        load(vb, wb, e + bd);
+        work(va, wa, e);
+        load(va, wa, e + 2 * bd);
+        work(vb, wb, e + bd);
     }
-    if (mode == 1) {
-        for (int i = threadIdx.x; i < nv; i += blockDim.x) gd->h2[i] = tot[i] * gd->scale[i];
-        return;
-    }
-    if (threadIdx.x != 0) return;
-    const int ld = GmresDev::LD;
-    double *H = gd->H;
-    for (int i = 0; i <= j; ++i) H[i + ld * j] = gd->h1[i] + gd->h2[i];
-    const double hn = sqrt(tot[0]);
-    H[j + 1 + ld * j] = hn;
-    gd->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-    for (int i = 0; i < j; ++i) {
-        const double a = H[i + ld * j], b = H[i + 1 + ld * j];
-        H[i + ld * j] = gd->cs[i] * a + gd->sn[i] * b;
-        H[i + 1 + ld * j] = -gd->sn[i] * a + gd->cs[i] * b;
-    }
-    const double a = H[j + ld * j], b = H[j + 1 + ld * j];
-    const double rr = hypot(a, b);
-    const double cs = rr > 0.0 ? a / rr : 1.0, sn = rr > 0.0 ? b / rr : 0.0;
-    gd->cs[j] = cs;
-    gd->sn[j] = sn;
-    H[j + ld * j] = rr;
-    H[j + 1 + ld * j] = 0.0;
-    gd->g[j + 1] = -sn * gd->g[j];
-    gd->g[j] = cs * gd->g[j];
-    gd->jd = j + 1;
-    const double est = fabs(gd->g[j + 1]);
-    if (!isfinite(est) || !isfinite(hn)) {
-        gd->breakdown = 1;
-        gd->done = 1;
-    } else if (est <= gd->target || hn == 0.0) {
-        gd->done = 1;
-    }
+    block_reduce_store<MAXV>(acc, MODE == PASS_UPD_NRM ? 1 : nv, partials + (long long)blockIdx.x * RB_STRIDE);
+    if (last_block_arrived(&gd->arrived)) arnoldi_finish(partials, gridDim.x, nv, gd, MODE, nv - 1);
 }
 
 // start a cycle: beta = sqrt(red), g = beta e1, scale[0] = 1/beta, target = rel_factor * beta
@@ -211,25 +277,59 @@ static llg_status residual_async(llg_ctx *c, const double *b, const double *t, d
     return cuda_check(c, cudaGetLastError(), "residual");
 }
 
+// blocks of an Arnoldi pass: every SM filled to the kernel's occupancy (one wave),
+// capped by the capacity of the partial-sum buffer
+template <typename K> static int arnoldi_grid(llg_ctx *c, K kern) {
+    for (const auto &p : c->occ)
+        if (p.first == (const void *)kern) return p.second;
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, RB_THREADS, 0) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    const int nb = std::min(per * c->sm_count, partial_capacity(c));
+    c->occ.push_back({(const void *)kern, nb});
+    return nb;
+}
+
+// One instantiation per basis count up to 32 (restart 30 needs 31): a kernel compiled
+// for more vectors than it uses still spends FP64 issue slots on the predicated-off
+// multiply-adds, which costs up to half of a pass.  Above 32, buckets of 8.
 template <int MAXV>
 static void launch_pass(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const double *win, double *wout,
                         long long n) {
-    const int nb = reduction_blocks(c);
     GmresDev *gd = c->gdev;
-    if (mode == PASS_DOT)
-        arnoldi_pass<MAXV, PASS_DOT><<<nb, RB_THREADS, 0, c->stream>>>(V, ldv, nv, gd, win, wout, n, c->red);
-    else if (mode == PASS_UPD_DOT)
-        arnoldi_pass<MAXV, PASS_UPD_DOT><<<nb, RB_THREADS, 0, c->stream>>>(V, ldv, nv, gd, win, wout, n, c->red);
-    else
-        arnoldi_pass<MAXV, PASS_UPD_NRM><<<nb, RB_THREADS, 0, c->stream>>>(V, ldv, nv, gd, win, wout, n, c->red);
+#define LLG_AP(KERN)                                                                      \
+    {                                                                                     \
+        auto k = KERN;                                                                    \
+        const int nb = arnoldi_grid(c, k);                                                \
+        k<<<nb, RB_THREADS, 0, c->stream>>>(V, ldv, nv, gd, win, wout, n, c->red);        \
+        return;                                                                           \
+    }
+    if constexpr (MAXV <= 16) {
+        if (mode == PASS_DOT) LLG_AP((arnoldi_pass_pipe<MAXV, PASS_DOT>))
+        if (mode == PASS_UPD_NRM) LLG_AP((arnoldi_pass_pipe<MAXV, PASS_UPD_NRM>))
+    }
+    if (mode == PASS_DOT) LLG_AP((arnoldi_pass<MAXV, PASS_DOT>))
+    if (mode == PASS_UPD_DOT) LLG_AP((arnoldi_pass<MAXV, PASS_UPD_DOT>))
+    LLG_AP((arnoldi_pass<MAXV, PASS_UPD_NRM>))
+#undef LLG_AP
 }
 
 static void pass_dispatch_raw(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const double *win, double *wout,
                               long long n) {
-    if (nv <= 4) launch_pass<4>(c, mode, V, ldv, nv, win, wout, n);
-    else if (nv <= 8) launch_pass<8>(c, mode, V, ldv, nv, win, wout, n);
-    else if (nv <= 16) launch_pass<16>(c, mode, V, ldv, nv, win, wout, n);
-    else if (nv <= 32) launch_pass<32>(c, mode, V, ldv, nv, win, wout, n);
+#define LLG_NV(K) case K: return launch_pass<K>(c, mode, V, ldv, nv, win, wout, n);
+    switch (nv) {
+        LLG_NV(1) LLG_NV(2) LLG_NV(3) LLG_NV(4) LLG_NV(5) LLG_NV(6) LLG_NV(7) LLG_NV(8)
+        LLG_NV(9) LLG_NV(10) LLG_NV(11) LLG_NV(12) LLG_NV(13) LLG_NV(14) LLG_NV(15) LLG_NV(16)
+        LLG_NV(17) LLG_NV(18) LLG_NV(19) LLG_NV(20) LLG_NV(21) LLG_NV(22) LLG_NV(23) LLG_NV(24)
+        LLG_NV(25) LLG_NV(26) LLG_NV(27) LLG_NV(28) LLG_NV(29) LLG_NV(30) LLG_NV(31) LLG_NV(32)
+        default: break;
+    }
+#undef LLG_NV
+    if (nv <= 40) launch_pass<40>(c, mode, V, ldv, nv, win, wout, n);
+    else if (nv <= 48) launch_pass<48>(c, mode, V, ldv, nv, win, wout, n);
+    else if (nv <= 56) launch_pass<56>(c, mode, V, ldv, nv, win, wout, n);
     else launch_pass<64>(c, mode, V, ldv, nv, win, wout, n);
 }
 
@@ -247,14 +347,11 @@ static void pass_dispatch(llg_ctx *c, int mode, const double *V, long long ldv, 
 static llg_status arnoldi_step(llg_ctx *c, int j) {
     Workspace &w = c->ws;
     const long long n = w.n;
-    const int nb = reduction_blocks(c), nv = j + 1;
+    const int nv = j + 1;
     pass_dispatch(c, PASS_DOT, w.V, n, nv, w.W, nullptr, n, j);
-    arnoldi_reduce<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, nv, c->gdev, 0, j);
     pass_dispatch(c, PASS_UPD_DOT, w.V, n, nv, w.W, w.W, n, j);
-    arnoldi_reduce<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, nv, c->gdev, 1, j);
     pass_dispatch(c, PASS_UPD_NRM, w.V, n, nv, w.W, w.V + (long long)(j + 1) * n, n, j);
-    arnoldi_reduce<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, nv, c->gdev, 2, j);
-    c->launches += 6;
+    c->launches += 3;
     return cuda_check(c, cudaGetLastError(), "arnoldi");
 }
 

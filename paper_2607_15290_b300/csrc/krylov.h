@@ -22,6 +22,8 @@ struct GmresDev {
     double y[MAXM], coef[MAXM];
     double scale[LD];      // 1 / ||V_i|| of the stored (unnormalised) basis vectors
     double h1[MAXM], h2[MAXM];
+    unsigned int arrived;  // blocks of the running Arnoldi pass that have stored their partial sums
+    int pad2;
 };
 static constexpr size_t GMRES_HEADER_BYTES = 32;
 

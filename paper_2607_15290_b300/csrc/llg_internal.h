@@ -118,6 +118,7 @@ struct llg_ctx {
     std::vector<ProfEntry> prof;
     size_t prof_used = 0;
     int prof_open = -1;
+    std::vector<std::pair<const void *, int>> occ;   // grid size per Arnoldi kernel (one full wave)
 };
 
 namespace llg {
@@ -140,6 +141,7 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
 
 // reductions.cu / krylov.cu
 int reduction_blocks(llg_ctx *c);
+int partial_capacity(llg_ctx *c);   // blocks the partial-sum buffer red holds
 llg_status dot_async(llg_ctx *c, const double *a, const double *b, long long n, double *dst_dev);
 
 }  // namespace llg
