@@ -295,10 +295,108 @@ __device__ __forceinline__ void sum_chunks_buf(const EnsProb &P, const double *b
     }
 }
 
+// ---------------------------------------------------------------- exact-count FP64 loops
+
+// The FP64 loops over the basis are compiled for the exact number of vectors NV: a loop
+// compiled for ENS_MAXM with the surplus predicated off still spends FP64 issue slots
+// on the skipped multiply-adds.  ENS_NV(nv, CALL) runs CALL with constexpr NVC = nv.
+#define ENS_NV(nv, CALL)                                                                              \
+    do {                                                                                              \
+        switch (nv) {                                                                                 \
+            ENS_NV_CASES(CALL)                                                                        \
+            default: break;                                                                           \
+        }                                                                                             \
+    } while (0)
+#define ENS_NV_CASES(CALL_)                                                                           \
+    ENS_NV_C(1, CALL_) ENS_NV_C(2, CALL_) ENS_NV_C(3, CALL_) ENS_NV_C(4, CALL_) ENS_NV_C(5, CALL_)     \
+    ENS_NV_C(6, CALL_) ENS_NV_C(7, CALL_) ENS_NV_C(8, CALL_) ENS_NV_C(9, CALL_) ENS_NV_C(10, CALL_)    \
+    ENS_NV_C(11, CALL_) ENS_NV_C(12, CALL_) ENS_NV_C(13, CALL_) ENS_NV_C(14, CALL_) ENS_NV_C(15, CALL_) \
+    ENS_NV_C(16, CALL_) ENS_NV_C(17, CALL_) ENS_NV_C(18, CALL_) ENS_NV_C(19, CALL_) ENS_NV_C(20, CALL_) \
+    ENS_NV_C(21, CALL_) ENS_NV_C(22, CALL_) ENS_NV_C(23, CALL_) ENS_NV_C(24, CALL_) ENS_NV_C(25, CALL_) \
+    ENS_NV_C(26, CALL_) ENS_NV_C(27, CALL_) ENS_NV_C(28, CALL_) ENS_NV_C(29, CALL_) ENS_NV_C(30, CALL_) \
+    ENS_NV_C(31, CALL_) ENS_NV_C(32, CALL_)
+#define ENS_NV_C(K, CALL_) case K: { constexpr int NVC = K; CALL_; } break;
+
+// per-block sums of acc[0..NV) into part[0..NV) (warp shuffles, then the warps in order;
+// red: ENS_THREADS / 32 rows of ENS_MAXM shared doubles)
+template <int NV>
+__device__ __forceinline__ void ens_reduce_store(double (&acc)[NV], double *part, double (*red)[ENS_MAXM]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NV; i += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < ENS_THREADS / 32; ++w) t += red[w][i];
+        part[i] = t;
+    }
+    __syncthreads();
+}
+
+// part[i] = this block's share of V_i . w
+template <int NV>
+__device__ __forceinline__ void ens_dots(const EnsProb &P, long long lo, long long hi, double *part, double (*red)[ENS_MAXM]) {
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (long long e = lo + threadIdx.x; e < hi; e += ENS_THREADS) {
+        const double w = P.W[e];
+        double vv[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) vv[i] = __ldcs(&P.V[(long long)i * P.n4 + e]);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += vv[i] * w;
+    }
+    ens_reduce_store<NV>(acc, part, red);
+}
+
+// w <- w - V cf written to out; part = this block's share of V^T w (DOT) or of |w|^2
+template <int NV, bool DOT>
+__device__ __forceinline__ void ens_update(const EnsProb &P, long long lo, long long hi, const double *cf, double *out,
+                                           double *part, double (*red)[ENS_MAXM]) {
+    constexpr int NA = DOT ? NV : 1;
+    double acc[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) acc[i] = 0.0;
+    for (long long e = lo + threadIdx.x; e < hi; e += ENS_THREADS) {
+        double w = P.W[e];
+        double vv[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) vv[i] = P.V[(long long)i * P.n4 + e];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) w -= cf[i] * vv[i];
+        out[e] = w;
+        if (DOT) {
+#pragma unroll
+            for (int i = 0; i < NA; ++i) acc[i] += vv[i] * w;
+        } else {
+            acc[0] += w * w;
+        }
+    }
+    ens_reduce_store<NA>(acc, part, red);
+}
+
+// x += Z y over the NV basis vectors of the cycle
+template <int NV>
+__device__ __forceinline__ void ens_xupdate(const EnsProb &P, long long lo, long long hi, const double *ys) {
+    for (long long e = lo + threadIdx.x; e < hi; e += ENS_THREADS) {
+        double v = P.x[e];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v += ys[i] * (double)P.Z[(long long)i * P.n4 + e];
+        P.x[e] = v;
+    }
+}
+
 // ---------------------------------------------------------------- the persistent kernel
 
 __global__ void __launch_bounds__(ENS_THREADS, 2) ens_kernel(EnsArgs A) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double s_red[ENS_THREADS / 32][ENS_MAXM];   // block sums of the Gram-Schmidt passes
     EnsState *S = A.st;
     const int tid = threadIdx.x;
 
@@ -450,16 +548,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ens_kernel(EnsArgs A) {
                     if (S[p].cyc_done) return;
                     long long lo, hi;
                     chunk_range(P, ch, lo, hi);
-                    double acc[ENS_MAXM];
-#pragma unroll
-                    for (int i = 0; i < ENS_MAXM; ++i) acc[i] = 0.0;
-                    for (long long e = lo + tid; e < hi; e += ENS_THREADS) {
-                        const double w = P.W[e];
-#pragma unroll
-                        for (int i = 0; i < ENS_MAXM; ++i)
-                            if (i < nv) acc[i] += __ldcs(&P.V[(long long)i * P.n4 + e]) * w;
-                    }
-                    block_reduce_store<ENS_MAXM>(acc, nv, A.partials + (P.ch0 + ch) * 32);
+                    ENS_NV(nv, (ens_dots<NVC>(P, lo, hi, A.partials + (P.ch0 + ch) * 32, s_red)));
                     if (last_chunk(A, p)) {
                         __shared__ double tot1[ENS_MAXM];
                         sum_chunks_buf(P, A.partials, nv, tot1);
@@ -478,20 +567,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ens_kernel(EnsArgs A) {
                     __shared__ double cf[ENS_MAXM];
                     if (tid < nv) cf[tid] = S[p].h1[tid] * S[p].scale[tid];
                     __syncthreads();
-                    double acc[ENS_MAXM];
-#pragma unroll
-                    for (int i = 0; i < ENS_MAXM; ++i) acc[i] = 0.0;
-                    for (long long e = lo + tid; e < hi; e += ENS_THREADS) {
-                        double w = P.W[e];
-#pragma unroll
-                        for (int i = 0; i < ENS_MAXM; ++i)
-                            if (i < nv) w -= cf[i] * P.V[(long long)i * P.n4 + e];
-                        P.W[e] = w;
-#pragma unroll
-                        for (int i = 0; i < ENS_MAXM; ++i)
-                            if (i < nv) acc[i] += P.V[(long long)i * P.n4 + e] * w;
-                    }
-                    block_reduce_store<ENS_MAXM>(acc, nv, A.partB + (P.ch0 + ch) * 32);
+                    ENS_NV(nv, (ens_update<NVC, true>(P, lo, hi, cf, P.W, A.partB + (P.ch0 + ch) * 32, s_red)));
                     if (last_chunk(A, p)) {
                         __shared__ double tot2[ENS_MAXM];
                         sum_chunks_buf(P, A.partB, nv, tot2);
@@ -511,18 +587,8 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ens_kernel(EnsArgs A) {
                     __shared__ double cf2[ENS_MAXM];
                     if (tid < nv) cf2[tid] = S[p].h2[tid] * S[p].scale[tid];
                     __syncthreads();
-                    double acc[ENS_MAXM];
-                    acc[0] = 0.0;
                     double *vn = P.V + (long long)(j + 1) * P.n4;
-                    for (long long e = lo + tid; e < hi; e += ENS_THREADS) {
-                        double w = P.W[e];
-#pragma unroll
-                        for (int i = 0; i < ENS_MAXM; ++i)
-                            if (i < nv) w -= cf2[i] * P.V[(long long)i * P.n4 + e];
-                        vn[e] = w;
-                        acc[0] += w * w;
-                    }
-                    block_reduce_store<ENS_MAXM>(acc, 1, A.partC + (P.ch0 + ch) * 32);
+                    ENS_NV(nv, (ens_update<NVC, false>(P, lo, hi, cf2, vn, A.partC + (P.ch0 + ch) * 32, s_red)));
                     if (last_chunk(A, p)) {
                         __shared__ double tot3[ENS_MAXM];
                         sum_chunks_buf(P, A.partC, 1, tot3);
@@ -588,13 +654,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ens_kernel(EnsArgs A) {
                 __shared__ double ys[ENS_MAXM];
                 if (tid < jd) ys[tid] = S[p].y[tid];
                 __syncthreads();
-                for (long long e = lo + tid; e < hi; e += ENS_THREADS) {
-                    double v = P.x[e];
-#pragma unroll
-                    for (int i = 0; i < ENS_MAXM; ++i)
-                        if (i < jd) v += ys[i] * (double)P.Z[(long long)i * P.n4 + e];
-                    P.x[e] = v;
-                }
+                ENS_NV(jd, (ens_xupdate<NVC>(P, lo, hi, ys)));
                 __syncthreads();
             });
             if (!bar_sync(A.bar, __LINE__)) return;
