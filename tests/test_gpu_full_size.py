@@ -1,0 +1,147 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py times
+(autotuned axis-pass shapes).
+
+* Element-wise: FFT--HSS applies (FP64 and FP32) and saddle matvecs at 1024^2, 128^3 and
+  256^3 against the oracle, which runs its radix-2 FFT mode there (pinned against the
+  naive DFT on small grids); tolerances as in test_gpu_parity (1e-12 FP64, 2e-5 FP32).
+* Properties that hold at any size: for the 128^3 midpoint workload and the 1024^2
+  midpoint workload (smooth and broadband fields) solved tightly, nodal length drift
+  <= 1e-12, the exact discrete dissipation identity, the energy against the oracle's; and
+  the solution at GMRES rtol 1e-10 against a tightly converged one to 1e-8.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2607_15290_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2607_15290_b300 as L  # noqa: E402
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def gpu(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture
+def oracle_fft():
+    O.set_transform(O.FFT)
+    yield
+    O.set_transform(O.DFT)
+
+
+def k_explicit(alpha, n, dim):
+    """explicit exchange limit 2 alpha / (Chat max|xi|^2) on the unit cell, spectral symbol"""
+    return 2 * alpha / ((1 + alpha ** 2) * dim * (math.pi * n) ** 2)
+
+
+def workload(n):
+    """(alpha, k) of the 1024^2 midpoint workload (13.3x the limit) and of the 128^3 / 256^3
+    one (4x)"""
+    if len(n) == 2:
+        return 0.02, 13.3 * k_explicit(0.02, n[0], 2)
+    return 0.1, 4 * k_explicit(0.1, n[0], 3)
+
+
+@pytest.mark.parametrize("n", [(1024, 1024), (128, 128, 128)], ids=["1024sq", "128cube"])
+def test_full_size_apply_and_matvec(oracle_fft, n):
+    og = O.Grid(n)
+    ctx = L.Context(n)
+    ctx.autotune()
+    m = I.smooth2d(n) if len(n) == 2 else I.smooth3d(n)
+    p = I.random_saddle_vector(n, seed=121)
+    alpha, k = workload(n)
+    po = O.Params(alpha=alpha, k=k, theta=0.5, lam=0.5, h=(0.0, 0.0, 0.5))
+    pl = L.Params(alpha=alpha, k=k, theta=0.5, lam=0.5, h_ext=(0.0, 0.0, 0.5))
+    gm, gp = gpu(m), gpu(p)
+    ref = O.ffthss_apply(og, po, m, p)
+    assert rel(host(L.llg_ffthss_apply(ctx, pl, gm, gp)), ref) <= 1e-12
+    got32 = host(L.llg_ffthss_apply_f32(ctx, pl, gpu(m, torch.float32), gpu(p, torch.float32)))
+    assert rel(got32, ref) <= 2e-5
+    ref_s = O.saddle_apply(og, po, m, p)
+    assert rel(host(L.llg_saddle_apply(ctx, pl, gm, gp)), ref_s) <= 1e-12
+    ctx.close()
+
+
+def test_full_size_256cube_fp32_apply(oracle_fft):
+    n = (256, 256, 256)
+    og = O.Grid(n)
+    ctx = L.Context(n)
+    ctx.autotune(fp64=False, fp32=True)
+    m = I.smooth3d(n)
+    p = I.random_saddle_vector(n, seed=122)
+    alpha, k = workload(n)
+    po = O.Params(alpha=alpha, k=k, theta=0.5, lam=0.5)
+    pl = L.Params(alpha=alpha, k=k, theta=0.5, lam=0.5)
+    ref = O.ffthss_apply(og, po, m, p)
+    got = host(L.llg_ffthss_apply_f32(ctx, pl, gpu(m, torch.float32), gpu(p, torch.float32)))
+    assert rel(got, ref) <= 2e-5
+    ctx.close()
+
+
+def midpoint_checks(ctx, og, po, pl, m0, steps, opts):
+    mg, vg = gpu(m0), None
+    for _ in range(steps):
+        e_prev = O.energy(og, po, host(mg))
+        mg, xg, info = L.llg_step_midpoint(ctx, pl, opts, mg, vg)
+        vg = xg[:3].contiguous()
+        assert info["rel_res_true"] <= opts.rtol, info
+        assert info["max_len_drift"] <= 1e-12, info
+        assert abs(info["energy_before"] - e_prev) <= 1e-11 * abs(e_prev)
+        assert abs(info["energy_after"] - O.energy(og, po, host(mg))) <= 1e-11 * abs(e_prev)
+        assert abs(info["dissipation_residual"]) <= 1e-9 * abs(e_prev)
+    return mg
+
+
+def test_full_size_midpoint_128cube(oracle_fft):
+    """The bench workload (FP32-flexible FGMRES(30)): solved tightly, the invariants hold at
+    full size; at the workload's rtol 1e-10 the step's velocity matches the tight one to 1e-8."""
+    n = (128, 128, 128)
+    og = O.Grid(n)
+    ctx = L.Context(n)
+    ctx.autotune()
+    alpha, k = workload(n)
+    po = O.Params(alpha=alpha, k=k, theta=0.5, lam=0.5, h=(0.0, 0.0, 0.5))
+    pl = L.Params(alpha=alpha, k=k, theta=0.5, lam=0.5, h_ext=(0.0, 0.0, 0.5))
+    m0 = I.smooth3d(n)
+    tight = L.Opts(restart=30, rtol=1e-12, picard_tol=1e-12, picard_max=50, precision=L.PREC_FP32_FLEX,
+                   diagnostics=1)
+    midpoint_checks(ctx, og, po, pl, m0, 2, tight)
+    bench_opts = L.Opts(restart=30, rtol=1e-10, picard_tol=1e-10, picard_max=50, precision=L.PREC_FP32_FLEX)
+    _, x_b, info_b = L.llg_step_midpoint(ctx, pl, bench_opts, gpu(m0), None)
+    _, x_t, _ = L.llg_step_midpoint(ctx, pl, L.Opts(restart=30, rtol=1e-13, picard_tol=1e-13, picard_max=60,
+                                                    precision=L.PREC_FP32_FLEX), gpu(m0), None)
+    assert info_b["rel_res_true"] <= 1e-10
+    assert rel(host(x_b)[:3], host(x_t)[:3]) <= 1e-8
+    ctx.close()
+
+
+@pytest.mark.parametrize("field", ["smooth", "broadband"])
+def test_full_size_midpoint_1024sq(oracle_fft, field):
+    """The 1024^2 FP64 midpoint workload (alpha 0.02, 13.3x the explicit limit), both fields."""
+    n = (1024, 1024)
+    og = O.Grid(n)
+    ctx = L.Context(n)
+    ctx.autotune(fp64=True, fp32=False)
+    alpha, k = workload(n)
+    po = O.Params(alpha=alpha, k=k, theta=0.5, lam=0.5)
+    pl = L.Params(alpha=alpha, k=k, theta=0.5, lam=0.5)
+    m0 = I.smooth2d(n) if field == "smooth" else I.broadband(n, seed=20260725)
+    opts = L.Opts(restart=30, rtol=1e-12, picard_tol=1e-12, picard_max=60, diagnostics=1)
+    midpoint_checks(ctx, og, po, pl, m0, 2, opts)
+    ctx.close()
