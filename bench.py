@@ -48,6 +48,14 @@ def peaks():
         return {"hbm_gbs": 6400.0, "fallback": True}
 
 
+# DRAM traffic per launch of the dominant class (dram__bytes_read.sum + dram__bytes_write.sum),
+# from one ncu capture of 90 arnoldi_pass launches of this workload at 128^3 (launches that
+# returned at once left out); to be re-taken whenever the Arnoldi kernels change.
+ARNOLDI_TRAFFIC_BYTES = 385.9e6
+ARNOLDI_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 63 non-empty "
+                        "arnoldi_pass launches of this workload (exact-count kernels, fused reduction)")
+
+
 def workload_params(n=128):
     import numpy as np
     alpha = 0.1
@@ -277,7 +285,8 @@ def main():
     if args.roofline_class == "arnoldi":
         achieved = prof["flops"] / (prof["ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
+                "frac": achieved / fp64_peak, "traffic": ARNOLDI_TRAFFIC_BYTES if args.n == 128 else None,
+                "traffic_note": ARNOLDI_TRAFFIC_NOTE, "algorithmic_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
                 "kernel": "arnoldi_pass (FP64 CGS2 multi-dot/update)", "launches": prof["launches"],
                 "avg_launch_ms": avg_ms, "hbm_gbs_at_algorithmic_bytes": prof["bytes"] / (prof["ms"] / 1e3) / 1e9,
                 "peak_source": "FP64 FMA rate measured live on this device (llg_probe_fma_rate); nominal 1.25"}
