@@ -47,7 +47,7 @@ class _Params(C.Structure):
     _fields_ = [("alpha", C.c_double), ("c_ex", C.c_double), ("k", C.c_double),
                 ("theta", C.c_double), ("lam", C.c_double), ("h", C.c_double * 3),
                 ("exchange", C.c_int), ("k_an", C.c_double), ("e_an", C.c_double * 3),
-                ("demag", C.c_int)]
+                ("demag", C.c_int), ("h_field", C.POINTER(C.c_double))]
 
 
 class _Opts(C.Structure):
@@ -106,6 +106,7 @@ class Params:
     k_an: float = 0.0
     e_an: tuple = (0.0, 0.0, 1.0)
     demag: int = 0
+    h_field: object = None   # optional (3, *grid shape) nodal applied field, added to h
 
     def c(self):
         p = _Params()
@@ -114,6 +115,10 @@ class Params:
             p.h[i] = self.h[i]
             p.e_an[i] = self.e_an[i]
         p.exchange, p.k_an, p.demag = self.exchange, self.k_an, self.demag
+        if self.h_field is not None:
+            hf = np.ascontiguousarray(np.asarray(self.h_field, dtype=np.float64))
+            p._hf = hf   # keeps the array alive as long as the struct
+            p.h_field = hf.ctypes.data_as(C.POINTER(C.c_double))
         return p
 
 

@@ -457,7 +457,7 @@ static void demag_field(const orc_grid *g, const double *m, double *hd) {
 void orc_h_low(const orc_grid *g, const orc_params *p, const double *m, double *hl) {
     long N = nodes_of(g);
     for (int c = 0; c < 3; ++c)
-        for (long j = 0; j < N; ++j) hl[c * N + j] = p->h[c];
+        for (long j = 0; j < N; ++j) hl[c * N + j] = p->h[c] + (p->h_field ? p->h_field[c * N + j] : 0.0);
     if (p->k_an != 0.0) {
         for (long j = 0; j < N; ++j) {
             double em = p->e_an[0] * m[j] + p->e_an[1] * m[N + j] + p->e_an[2] * m[2 * N + j];
@@ -472,7 +472,7 @@ void orc_h_low(const orc_grid *g, const orc_params *p, const double *m, double *
     }
 }
 
-/* g_N(m) = (1/N_g) sum_j [ c_ex/2 m.(-Lap m) - h.m + k_an (1 - (e.m)^2) - 1/2 m.h_dem ] */
+/* g_N(m) = (1/N_g) sum_j [ c_ex/2 m.(-Lap m) - h_j.m + k_an (1 - (e.m)^2) - 1/2 m.h_dem ], h_j = h + h_field_j */
 double orc_energy(const orc_grid *g, const orc_params *p, const double *m) {
     long N = nodes_of(g);
     double *lap = malloc(sizeof(double) * 3 * N);
@@ -486,7 +486,10 @@ double orc_energy(const orc_grid *g, const orc_params *p, const double *m) {
     for (long j = 0; j < N; ++j) {
         double mj[3] = { m[j], m[N + j], m[2 * N + j] };
         double ej = 0.0;
-        for (int c = 0; c < 3; ++c) ej += 0.5 * p->c_ex * mj[c] * lap[c * N + j] - p->h[c] * mj[c];
+        for (int c = 0; c < 3; ++c) {
+            double hc = p->h[c] + (p->h_field ? p->h_field[c * N + j] : 0.0);
+            ej += 0.5 * p->c_ex * mj[c] * lap[c * N + j] - hc * mj[c];
+        }
         if (p->k_an != 0.0) {
             double em = p->e_an[0] * mj[0] + p->e_an[1] * mj[1] + p->e_an[2] * mj[2];
             ej += p->k_an * (1.0 - em * em);

@@ -44,6 +44,7 @@ typedef struct {
     double k_an;    /* anisotropy energy k_an (1 - (e.m)^2), 0 = off */
     double e_an[3]; /* easy axis */
     int demag;      /* 1 = periodic zero-mean demagnetising field */
+    const double *h_field; /* optional nodal applied field (3 planes), added to h; NULL = none */
 } orc_params;
 
 typedef struct {

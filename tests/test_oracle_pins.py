@@ -390,6 +390,45 @@ def test_energy_pins_3d_micromagnetic():
     assert drift <= 1e-10
 
 
+def manufactured_error(scheme, k, n=(64, 64), alpha=0.2, T=0.1):
+    """Run the oracle's Euler or midpoint scheme on the manufactured solution of Sec. 4.2 with
+    its forcing (Euler at t_{n+1}, midpoint at t_{n+1/2}) and return the mean over the three
+    components of the max-norm error at T."""
+    g = O.Grid(n, (2 * np.pi, 2 * np.pi))
+    steps = int(round(T / k))
+    m, _ = I.manufactured2d(n, 0.0, alpha)
+    opts = O.Opts(restart=50, rtol=1e-10, picard_tol=1e-10)
+    vprev = None
+    for s in range(steps):
+        t = s * k
+        if scheme == "euler":
+            _, f = I.manufactured2d(n, t + k, alpha)
+            m, _, _ = O.step_euler(g, O.Params(alpha=alpha, k=k, theta=1.0, lam=0.5, h_field=f), opts, m)
+        else:
+            _, f = I.manufactured2d(n, t + 0.5 * k, alpha)
+            m, x, _ = O.step_midpoint(g, O.Params(alpha=alpha, k=k, theta=0.5, lam=0.5, h_field=f), opts, m, vprev)
+            vprev = x[:3]
+    me, _ = I.manufactured2d(n, steps * k, alpha)
+    return float(np.mean([np.abs(m[c] - me[c]).max() for c in range(3)]))
+
+
+@pytest.mark.parametrize("scheme,order", [("euler", 1), ("midpoint", 2)])
+def test_temporal_convergence_printed_errors(scheme, order):
+    """The errors the paper prints for its manufactured solution (Sec. 4.2), to every printed
+    digit, at k = 1e-2 and 1.25e-3; the observed order between those two step sizes within
+    1e-3 of one (Euler) and two (midpoint)."""
+    G = GOLD["temporal_convergence"]
+    O.set_transform(O.FFT)
+    try:
+        errs = [manufactured_error(scheme, k, alpha=G["alpha"], T=G["T"]) for k in G["k"]]
+    finally:
+        O.set_transform(O.DFT)
+    for k, e, val, tol in zip(G["k"], errs, G[scheme]["value"], G[scheme]["tol"]):
+        assert abs(e - val) <= tol, (k, e, val)
+    observed = math.log2(errs[0] / errs[1]) / math.log2(G["k"][0] / G["k"][1])
+    assert abs(observed - order) <= G["order_tol"], (observed, errs)
+
+
 # ------------------------------------------------------------------ adjoint vs central finite differences
 
 def test_adjoint_matches_central_differences():
