@@ -61,11 +61,17 @@ typedef struct {
 
 /* alpha > 0 damping; c_ex > 0 normalised exchange coefficient (paper: 1);
    k >= 0 time step; theta in {1, 1/2} (Euler / midpoint; steps set it themselves);
-   lambda > 0 HSS shift; h_ext uniform applied field; exchange = LLG_EX_* */
+   lambda > 0 HSS shift; h_ext uniform applied field; exchange = LLG_EX_*;
+   h_field: optional per-node applied field added to h_ext in the lower-order field h_low
+   (DEVICE, 3 FP64 planes, caller-owned, read by the right-hand side and the energy; NULL =
+   none).  A time-dependent field (e.g. a manufactured-solution forcing, Sec. 4.2) is passed
+   per step, sampled where the scheme samples h_low: t_{n+1} (Euler), t_{n+1/2} (midpoint).
+   The ensemble rejects a non-NULL h_field. */
 typedef struct {
     double alpha, c_ex, k, theta, lambda;
     double h_ext[3];
     int exchange;
+    const double *h_field;
 } llg_params;
 
 typedef struct {

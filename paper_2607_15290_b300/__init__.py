@@ -42,13 +42,25 @@ class Params:
     lam: float = 0.5
     h_ext: tuple = (0.0, 0.0, 0.0)
     exchange: int = EX_SPECTRAL
+    # optional per-node applied field added to h_ext: CUDA float64 tensor (3, *grid), passed
+    # per step (sampled at t_{n+1} for Euler, t_{n+1/2} for the midpoint scheme)
+    h_field: object = None
 
-    def c(self):
+    def c(self, ctx=None):
         p = _abi.Params()
         p.alpha, p.c_ex, p.k, p.theta, p.lam = self.alpha, self.c_ex, self.k, self.theta, self.lam
         for i in range(3):
             p.h_ext[i] = self.h_ext[i]
         p.exchange = self.exchange
+        p.h_field = None
+        if self.h_field is not None:
+            hf = self.h_field
+            torch = _torch()
+            if not (isinstance(hf, torch.Tensor) and hf.is_cuda and hf.dtype == torch.float64 and hf.is_contiguous()):
+                raise TypeError("h_field must be a contiguous CUDA float64 tensor of 3 planes")
+            if ctx is not None and hf.numel() != 3 * ctx.nodes:
+                raise ValueError(f"h_field has {hf.numel()} values, the grid needs {3 * ctx.nodes}")
+            p.h_field = hf.data_ptr()
         return p
 
 
@@ -161,14 +173,14 @@ class Context:
 
 def llg_saddle_apply(ctx: Context, prm: Params, m, x, transpose=False, out=None):
     y = out if out is not None else ctx.empty(4)
-    ctx._check(ctx.lib.llg_saddle_apply(ctx.h, C.byref(prm.c()), ctx._arr(m, 3), ctx._arr(x, 4), ctx._arr(y, 4),
+    ctx._check(ctx.lib.llg_saddle_apply(ctx.h, C.byref(prm.c(ctx)), ctx._arr(m, 3), ctx._arr(x, 4), ctx._arr(y, 4),
                                         int(transpose)))
     return y
 
 
 def llg_ffthss_apply(ctx: Context, prm: Params, m, p, transpose=False, out=None):
     z = out if out is not None else ctx.empty(4)
-    ctx._check(ctx.lib.llg_ffthss_apply(ctx.h, C.byref(prm.c()), ctx._arr(m, 3), ctx._arr(p, 4), ctx._arr(z, 4),
+    ctx._check(ctx.lib.llg_ffthss_apply(ctx.h, C.byref(prm.c(ctx)), ctx._arr(m, 3), ctx._arr(p, 4), ctx._arr(z, 4),
                                         int(transpose)))
     return z
 
@@ -176,7 +188,7 @@ def llg_ffthss_apply(ctx: Context, prm: Params, m, p, transpose=False, out=None)
 def llg_ffthss_apply_f32(ctx: Context, prm: Params, m, p, transpose=False, out=None):
     torch = _torch()
     z = out if out is not None else ctx.empty(4, torch.float32)
-    ctx._check(ctx.lib.llg_ffthss_apply_f32(ctx.h, C.byref(prm.c()), ctx._arr(m, 3, torch.float32),
+    ctx._check(ctx.lib.llg_ffthss_apply_f32(ctx.h, C.byref(prm.c(ctx)), ctx._arr(m, 3, torch.float32),
                                             ctx._arr(p, 4, torch.float32), ctx._arr(z, 4, torch.float32),
                                             int(transpose)))
     return z
@@ -184,7 +196,7 @@ def llg_ffthss_apply_f32(ctx: Context, prm: Params, m, p, transpose=False, out=N
 
 def llg_precond_saddle_apply(ctx: Context, prm: Params, m, x, out=None):
     z = out if out is not None else ctx.empty(4)
-    ctx._check(ctx.lib.llg_precond_saddle_apply(ctx.h, C.byref(prm.c()), ctx._arr(m, 3), ctx._arr(x, 4),
+    ctx._check(ctx.lib.llg_precond_saddle_apply(ctx.h, C.byref(prm.c(ctx)), ctx._arr(m, 3), ctx._arr(x, 4),
                                                 ctx._arr(z, 4)))
     return z
 
@@ -195,7 +207,7 @@ def llg_gmres_solve(ctx: Context, prm: Params, opts: Opts, m, b, x=None, raise_o
         x = ctx.empty(4)
         x.zero_()
     info = _abi.Info()
-    st = ctx.lib.llg_gmres_solve(ctx.h, C.byref(prm.c()), C.byref(opts.c()), ctx._arr(m, 3), ctx._arr(b, 4),
+    st = ctx.lib.llg_gmres_solve(ctx.h, C.byref(prm.c(ctx)), C.byref(opts.c()), ctx._arr(m, 3), ctx._arr(b, 4),
                                  ctx._arr(x, 4), C.byref(info))
     if raise_on_error:
         ctx._check(st, info.as_dict())
@@ -206,7 +218,7 @@ def llg_step_euler(ctx: Context, prm: Params, opts: Opts, m, m_next=None, x_out=
     m_next = m_next if m_next is not None else ctx.empty(3)
     x_out = x_out if x_out is not None else ctx.empty(4)
     info = _abi.Info()
-    st = ctx.lib.llg_step_euler(ctx.h, C.byref(prm.c()), C.byref(opts.c()), ctx._arr(m, 3), ctx._arr(m_next, 3),
+    st = ctx.lib.llg_step_euler(ctx.h, C.byref(prm.c(ctx)), C.byref(opts.c()), ctx._arr(m, 3), ctx._arr(m_next, 3),
                                 ctx._arr(x_out, 4), C.byref(info))
     if raise_on_error:
         ctx._check(st, info.as_dict())
@@ -219,7 +231,7 @@ def llg_step_midpoint(ctx: Context, prm: Params, opts: Opts, m, v_prev=None, m_n
     x_out = x_out if x_out is not None else ctx.empty(4)
     vp = C.c_void_p(0) if v_prev is None else ctx._arr(v_prev, 3)
     info = _abi.Info()
-    st = ctx.lib.llg_step_midpoint(ctx.h, C.byref(prm.c()), C.byref(opts.c()), ctx._arr(m, 3), vp,
+    st = ctx.lib.llg_step_midpoint(ctx.h, C.byref(prm.c(ctx)), C.byref(opts.c()), ctx._arr(m, 3), vp,
                                    ctx._arr(m_next, 3), ctx._arr(x_out, 4), C.byref(info))
     if raise_on_error:
         ctx._check(st, info.as_dict())
@@ -232,7 +244,7 @@ def llg_adjoint_step(ctx: Context, prm: Params, opts: Opts, m_n, x, mbar_next, m
     da = C.c_double(0.0)
     dh = (C.c_double * 3)(0.0, 0.0, 0.0)
     info = _abi.Info()
-    st = ctx.lib.llg_adjoint_step(ctx.h, C.byref(prm.c()), C.byref(opts.c()), ctx._arr(m_n, 3), ctx._arr(x, 4),
+    st = ctx.lib.llg_adjoint_step(ctx.h, C.byref(prm.c(ctx)), C.byref(opts.c()), ctx._arr(m_n, 3), ctx._arr(x, 4),
                                   ctx._arr(mbar_next, 3), ctx._arr(mbar_n, 3), C.byref(da), dh, C.byref(info))
     ctx._check(st, info.as_dict())
     return mbar_n, da.value, [dh[0], dh[1], dh[2]], info.as_dict()
@@ -298,5 +310,5 @@ class Ensemble:
 
 def llg_energy(ctx: Context, prm: Params, m):
     out = C.c_double(0.0)
-    ctx._check(ctx.lib.llg_energy(ctx.h, C.byref(prm.c()), ctx._arr(m, 3), C.byref(out)))
+    ctx._check(ctx.lib.llg_energy(ctx.h, C.byref(prm.c(ctx)), ctx._arr(m, 3), C.byref(out)))
     return out.value

@@ -45,7 +45,7 @@ class Grid(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("alpha", C.c_double), ("c_ex", C.c_double), ("k", C.c_double), ("theta", C.c_double),
-                ("lam", C.c_double), ("h_ext", C.c_double * 3), ("exchange", C.c_int)]
+                ("lam", C.c_double), ("h_ext", C.c_double * 3), ("exchange", C.c_int), ("h_field", C.c_void_p)]
 
 
 class Opts(C.Structure):

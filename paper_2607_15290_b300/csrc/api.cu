@@ -179,13 +179,19 @@ __global__ void k_mid_final(const double *__restrict__ m, const double *__restri
 
 // energy density sum: m . T - h . m, with T = (c_ex/2)(-Lap) m
 __global__ void k_energy_partials(const double *__restrict__ m, const double *__restrict__ T, double h0, double h1,
-                                  double h2, long long N, double *partials) {
+                                  double h2, const double *__restrict__ hf, long long N, double *partials) {
     long long lo, hi;
     block_chunk(N, lo, hi);
     double acc[1] = {0.0};
     for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
         const double a = m[j], b = m[N + j], c = m[2 * N + j];
-        acc[0] += a * T[j] + b * T[N + j] + c * T[2 * N + j] - (h0 * a + h1 * b + h2 * c);
+        double g0 = h0, g1 = h1, g2 = h2;
+        if (hf) {
+            g0 += hf[j];
+            g1 += hf[N + j];
+            g2 += hf[2 * N + j];
+        }
+        acc[0] += a * T[j] + b * T[N + j] + c * T[2 * N + j] - (g0 * a + g1 * b + g2 * c);
     }
     block_reduce_store<1>(acc, 1, partials + (long long)blockIdx.x * RB_STRIDE);
 }
@@ -380,12 +386,14 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
 }
 
 llg_status rhs_velocity(llg_ctx *c, const llg_params *p, const double *m, double *b) {
-    // f = Chat Lap_N m + (1 + alpha^2) h_ext ; multiplier row 0
+    // f = Chat Lap_N m + (1 + alpha^2) (h_ext + h_field) ; multiplier row 0
     auto io = make_io<double, double, double>(m, m, b, nullptr, p->lambda);
     const double s = 1.0 + p->alpha * p->alpha;
     io.fld[0] = s * p->h_ext[0];
     io.fld[1] = s * p->h_ext[1];
     io.fld[2] = s * p->h_ext[2];
+    io.hf = p->h_field;
+    io.hs = s;
     Symbol sym{0.0, -chat(p), 1.0 / (double)c->geo.N, 0, p->exchange};
     return spectral_chain<double, double, double>(c, IN_M, OUT_FIELD, io, sym);
 }
@@ -396,7 +404,7 @@ llg_status energy_async(llg_ctx *c, const llg_params *p, const double *m, double
     llg_status st = spectral_chain<double, double, double>(c, IN_M, OUT_PLAIN, io, sym);
     if (st != LLG_OK) return st;
     const int nb = reduction_blocks(c);
-    k_energy_partials<<<nb, RB_THREADS, 0, c->stream>>>(m, tmp, p->h_ext[0], p->h_ext[1], p->h_ext[2], c->geo.N, c->red);
+    k_energy_partials<<<nb, RB_THREADS, 0, c->stream>>>(m, tmp, p->h_ext[0], p->h_ext[1], p->h_ext[2], p->h_field, c->geo.N, c->red);
     k_sum_partials_n<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, 1, dst_dev);
     c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "energy");

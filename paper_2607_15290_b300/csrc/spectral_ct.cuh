@@ -258,9 +258,15 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
                 y[2 * Nn + j] = (TOut)(w3 + sg * (m1 * v2 - m2 * v1 + m3 * r));
                 y[3 * Nn + j] = (TOut)(-sg * (m1 * v1 + m2 * v2 + m3 * v3));
             } else if constexpr (OUT == OUT_FIELD) {
-                y[j] = (TOut)(w1 + io.fld[0]);
-                y[Nn + j] = (TOut)(w2 + io.fld[1]);
-                y[2 * Nn + j] = (TOut)(w3 + io.fld[2]);
+                T f1 = w1 + io.fld[0], f2 = w2 + io.fld[1], f3 = w3 + io.fld[2];
+                if (io.hf) {
+                    f1 += (T)(io.hs * io.hf[j]);
+                    f2 += (T)(io.hs * io.hf[Nn + j]);
+                    f3 += (T)(io.hs * io.hf[2 * Nn + j]);
+                }
+                y[j] = (TOut)f1;
+                y[Nn + j] = (TOut)f2;
+                y[2 * Nn + j] = (TOut)f3;
                 y[3 * Nn + j] = (TOut)0;
             } else if constexpr (OUT == OUT_PLAIN) {
                 y[j] = (TOut)w1; y[Nn + j] = (TOut)w2; y[2 * Nn + j] = (TOut)w3;
