@@ -48,6 +48,10 @@ enum { LLG_EX_SPECTRAL = 0, LLG_EX_FD2 = 1 };
    with the FFT--HSS application and its inner matvec in FP32 (Arnoldi, least squares,
    true residual and the solution update stay FP64) */
 enum { LLG_PREC_FP64 = 0, LLG_PREC_FP32_FLEX = 1 };
+/* left preconditioner of GMRES (Sec. 4.3 comparison): the split FFT--HSS preconditioner
+   (lambda I + S)^{-1} (lambda I + H)^{-1} of Sec. 3.2; the shifted symmetric part
+   (lambda I + H)^{-1} alone (Algorithm 1 on the velocity, r / lambda on the multiplier); none */
+enum { LLG_PC_FFTHSS = 0, LLG_PC_HERMITIAN = 1, LLG_PC_NONE = 2 };
 
 typedef struct llg_ctx llg_ctx;
 
@@ -82,6 +86,8 @@ typedef struct {
     int picard_max;     /* midpoint: cap on Picard iterations */
     double picard_tol;  /* midpoint: stop when ||v^p - v^{p-1}|| <= picard_tol ||v^p|| */
     int diagnostics;    /* steps: 1 = also compute energies and the dissipation residual */
+    int preconditioner; /* forward solves: LLG_PC_FFTHSS (default), LLG_PC_HERMITIAN, LLG_PC_NONE;
+                           transposed (adjoint) solves always use FFT--HSS */
 } llg_opts;
 
 typedef struct {

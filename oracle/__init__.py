@@ -25,6 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 SPECTRAL, FD2 = 0, 1
 DFT, FFT = 0, 1
+PC_FFTHSS, PC_HERMITIAN, PC_NONE = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -52,7 +53,8 @@ class _Params(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("restart", C.c_int), ("max_iters", C.c_int), ("rtol", C.c_double),
-                ("picard_max", C.c_int), ("picard_tol", C.c_double), ("use_dense", C.c_int)]
+                ("picard_max", C.c_int), ("picard_tol", C.c_double), ("use_dense", C.c_int),
+                ("precond", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -130,11 +132,13 @@ class Opts:
     picard_max: int = 50
     picard_tol: float = 1e-10
     use_dense: int = 0
+    precond: int = 0          # PC_FFTHSS, PC_HERMITIAN or PC_NONE
 
     def c(self):
         o = _Opts()
         o.restart, o.max_iters, o.rtol = self.restart, self.max_iters, self.rtol
         o.picard_max, o.picard_tol, o.use_dense = self.picard_max, self.picard_tol, self.use_dense
+        o.precond = self.precond
         return o
 
 

@@ -294,6 +294,15 @@ static void saddle_prec(void *c, const double *x, double *y) {
     saddle_ctx *s = c;
     orc_ffthss_apply(s->g, s->p, s->m, x, y, s->transpose);
 }
+/* (lambda I + H)^{-1}: H = diag(alpha + theta k Chat (-Lap), 0) is symmetric, so also its transpose */
+static void hermitian_prec(void *c, const double *x, double *y) {
+    saddle_ctx *s = c;
+    orc_hermitian_solve(s->g, s->p, x, y);
+}
+static void identity_prec(void *c, const double *x, double *y) {
+    saddle_ctx *s = c;
+    memcpy(y, x, sizeof(double) * 4 * nodes_of(s->g));
+}
 
 void orc_saddle_dense(const orc_grid *g, const orc_params *p, const double *m, double *A) {
     saddle_ctx s = { g, p, m, 0 };
@@ -414,7 +423,8 @@ int orc_gmres_solve(const orc_grid *g, const orc_params *p, const orc_opts *o, c
         if (info) { memset(info, 0, sizeof(*info)); info->converged = rc == 0; }
         return rc == 0 ? 0 : 1;
     }
-    return gmres_core(n, saddle_op, saddle_prec, &s, b, x, o->restart, o->max_iters, o->rtol,
+    orc_op prec = o->precond == ORC_PC_HERMITIAN ? hermitian_prec : (o->precond == ORC_PC_NONE ? identity_prec : saddle_prec);
+    return gmres_core(n, saddle_op, prec, &s, b, x, o->restart, o->max_iters, o->rtol,
                       info, res_hist, hist_len);
 }
 

@@ -54,7 +54,12 @@ typedef struct {
     int picard_max;   /* midpoint Picard cap */
     double picard_tol;/* midpoint Picard relative tolerance */
     int use_dense;    /* 1: solve each linear system by dense LU instead of GMRES */
+    int precond;      /* GMRES left preconditioner: ORC_PC_FFTHSS (default), _HERMITIAN, _NONE */
 } orc_opts;
+
+/* the split FFT--HSS preconditioner (lambda I + S)^{-1} (lambda I + H)^{-1}; the shifted
+   symmetric part (lambda I + H)^{-1} alone; no preconditioner (Sec. 4.3 comparison) */
+enum { ORC_PC_FFTHSS = 0, ORC_PC_HERMITIAN = 1, ORC_PC_NONE = 2 };
 
 typedef struct {
     int iters, restarts, picard_iters, converged;

@@ -17,7 +17,7 @@ import ctypes as C
 from dataclasses import dataclass, field
 
 from . import _abi
-from ._abi import EX_FD2, EX_SPECTRAL, PREC_FP32_FLEX, PREC_FP64
+from ._abi import EX_FD2, EX_SPECTRAL, PC_FFTHSS, PC_HERMITIAN, PC_NONE, PREC_FP32_FLEX, PREC_FP64
 
 __all__ = [
     "LLGError", "Params", "Opts", "Context", "EX_SPECTRAL", "EX_FD2", "PREC_FP64", "PREC_FP32_FLEX",
@@ -73,11 +73,13 @@ class Opts:
     picard_max: int = 50
     picard_tol: float = 1e-10
     diagnostics: int = 0
+    preconditioner: int = PC_FFTHSS
 
     def c(self):
         o = _abi.Opts()
         o.restart, o.max_iters, o.rtol, o.precision = self.restart, self.max_iters, self.rtol, self.precision
         o.picard_max, o.picard_tol, o.diagnostics = self.picard_max, self.picard_tol, self.diagnostics
+        o.preconditioner = self.preconditioner
         return o
 
 

@@ -25,6 +25,7 @@ STATUS = {
 }
 EX_SPECTRAL, EX_FD2 = 0, 1
 PREC_FP64, PREC_FP32_FLEX = 0, 1
+PC_FFTHSS, PC_HERMITIAN, PC_NONE = 0, 1, 2
 
 # every symbol the header declares, in declaration order
 EXPORTS = [
@@ -50,7 +51,8 @@ class Params(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("restart", C.c_int), ("max_iters", C.c_int), ("rtol", C.c_double), ("precision", C.c_int),
-                ("picard_max", C.c_int), ("picard_tol", C.c_double), ("diagnostics", C.c_int)]
+                ("picard_max", C.c_int), ("picard_tol", C.c_double), ("diagnostics", C.c_int),
+                ("preconditioner", C.c_int)]
 
 
 class Problem(C.Structure):

@@ -104,6 +104,15 @@ __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, lo
         b[e] = (float)a[e];
 }
 
+// y = s a (s = *scale, or 1 when scale is NULL): the identity "preconditioner"
+template <typename TO>
+__global__ void k_scaled_copy(const double *__restrict__ a, const double *__restrict__ scale, TO *__restrict__ y,
+                              long long n) {
+    const double sc = scale ? *scale : 1.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        y[e] = (TO)(sc * a[e]);
+}
+
 // m^{n+1} = (m + k v) / |m + k v|, and max_i | |m^{n+1}_i| - |m^n_i| |
 __global__ void k_euler_update(const double *__restrict__ m, const double *__restrict__ v, double k, double *mn,
                                long long N, double *partials) {
@@ -265,6 +274,8 @@ llg_status check_opts(llg_ctx *c, const llg_opts *o) {
     if (o->precision != LLG_PREC_FP64 && o->precision != LLG_PREC_FP32_FLEX)
         return set_error(c, LLG_ERR_INVALID_ARG, "unknown precision");
     if (o->picard_max < 1 || !(o->picard_tol > 0)) return set_error(c, LLG_ERR_INVALID_ARG, "need picard_max >= 1 and picard_tol > 0");
+    if (o->preconditioner != LLG_PC_FFTHSS && o->preconditioner != LLG_PC_HERMITIAN && o->preconditioner != LLG_PC_NONE)
+        return set_error(c, LLG_ERR_INVALID_ARG, "unknown preconditioner");
     return LLG_OK;
 }
 
@@ -337,9 +348,25 @@ llg_status op_apply64(llg_ctx *c, const llg_params *p, double theta, const doubl
 }
 
 llg_status op_fused64(llg_ctx *c, const llg_params *p, double theta, const double *m, const double *x,
-                      const double *scale, double *y) {
+                      const double *scale, double *y, int plain_nodal = 0) {
     auto io = make_io<double, double, double>(m, x, y, scale, p->lambda);
+    io.plain_nodal = plain_nodal;
     return spectral_chain<double, double, double>(c, IN_FUSED, OUT_FUSED, io, sym_shifted_inverse(c, p, theta));
+}
+
+// the shifted symmetric part (lambda I + H)^{-1} alone (no nodal inverse)
+llg_status op_hermitian64(llg_ctx *c, const llg_params *p, double theta, const double *m, const double *x,
+                          const double *scale, double *y) {
+    auto io = make_io<double, double, double>(m, x, y, scale, p->lambda);
+    io.plain_nodal = 1;
+    return spectral_chain<double, double, double>(c, IN_V, OUT_APPLY, io, sym_shifted_inverse(c, p, theta));
+}
+
+template <typename TO>
+llg_status op_scaled_copy(llg_ctx *c, const double *x, const double *scale, TO *y) {
+    k_scaled_copy<TO><<<grid_blocks(c), RB_THREADS, 0, c->stream>>>(x, scale, y, 4 * c->geo.N);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "identity preconditioner");
 }
 
 llg_status check_nodes(llg_ctx *c, const double *m) {
@@ -365,16 +392,27 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
     if ((st = ensure_spec(c, true, flex)) != LLG_OK) return st;
     SolveOps ops;
     ops.matvec = [=](const double *xx, double *yy) { return op_matvec64(c, p, theta, m, xx, nullptr, yy, 0); };
+    const int pc = o->preconditioner;
     if (!flex) {
-        ops.prec = [=](const double *xx, const double *s, double *yy) { return op_apply64(c, p, theta, m, xx, s, yy, 0); };
-        ops.pop = [=](const double *xx, const double *s, double *yy) { return op_fused64(c, p, theta, m, xx, s, yy); };
+        if (pc == LLG_PC_NONE) {
+            ops.prec = [=](const double *xx, const double *s, double *yy) { return op_scaled_copy<double>(c, xx, s, yy); };
+            ops.pop = [=](const double *xx, const double *s, double *yy) { return op_matvec64(c, p, theta, m, xx, s, yy, 0); };
+        } else if (pc == LLG_PC_HERMITIAN) {
+            ops.prec = [=](const double *xx, const double *s, double *yy) { return op_hermitian64(c, p, theta, m, xx, s, yy); };
+            ops.pop = [=](const double *xx, const double *s, double *yy) { return op_fused64(c, p, theta, m, xx, s, yy, 1); };
+        } else {
+            ops.prec = [=](const double *xx, const double *s, double *yy) { return op_apply64(c, p, theta, m, xx, s, yy, 0); };
+            ops.pop = [=](const double *xx, const double *s, double *yy) { return op_fused64(c, p, theta, m, xx, s, yy); };
+        }
     } else {
         if ((st = ensure_m32(c)) != LLG_OK) return st;
         k_to_f32<<<grid_blocks(c), RB_THREADS, 0, c->stream>>>(m, c->m32, 3 * c->geo.N);
         c->launches++;
         const float *m32 = c->m32;
         ops.fprec = [=](const double *xx, const double *s, float *zz) {
+            if (pc == LLG_PC_NONE) return op_scaled_copy<float>(c, xx, s, zz);
             auto io = make_io<double, float, float>(m32, xx, zz, s, p->lambda);
+            io.plain_nodal = pc == LLG_PC_HERMITIAN;
             return spectral_chain<float, double, float>(c, IN_V, OUT_APPLY, io, sym_shifted_inverse(c, p, theta));
         };
         ops.fmatvec = [=](const float *zz, double *ww) {

@@ -60,6 +60,9 @@ struct NodalIO {
     const T *mn;           // m^n (3 planes)
     const T *vf;           // forward velocity v (3 planes) and r (1 plane, at vf + 3N)
     T half_k;              // k / 2
+    // OUT_APPLY / OUT_FUSED: 1 = skip the nodal 4x4 inverse (the shifted symmetric-part
+    // preconditioner (lambda I + H)^{-1} alone)
+    int plain_nodal;
     // OUT_FIELD only: optional per-node field added as hs * hf (3 FP64 planes)
     const double *hf;
     double hs;

@@ -237,16 +237,15 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
             const T w3 = reinterpret_cast<const T *>(&fbase[(3 * gq + 2) * LS + e])[rr];
             TOut *y = io.y;
             if constexpr (OUT == OUT_APPLY) {
-                T z1, z2, z3, z4;
-                nodal_inverse<T, false>(mv[k][0], mv[k][1], mv[k][2], io.lam, w1, w2, w3,
-                                        s * (T)xv[k][3] / io.lam, z1, z2, z3, z4);
+                T z1 = w1, z2 = w2, z3 = w3, z4 = s * (T)xv[k][3] / io.lam;
+                if (!io.plain_nodal)
+                    nodal_inverse<T, false>(mv[k][0], mv[k][1], mv[k][2], io.lam, w1, w2, w3, z4, z1, z2, z3, z4);
                 y[j] = (TOut)z1; y[Nn + j] = (TOut)z2; y[2 * Nn + j] = (TOut)z3; y[3 * Nn + j] = (TOut)z4;
             } else if constexpr (OUT == OUT_FUSED) {
                 const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];
                 const T v1 = s * (T)xv[k][0], v2 = s * (T)xv[k][1], v3 = s * (T)xv[k][2];
-                T z1, z2, z3, z4;
-                nodal_inverse<T, false>(m1, m2, m3, io.lam, v1 + w1, v2 + w2, v3 + w3,
-                                        -(m1 * v1 + m2 * v2 + m3 * v3) / io.lam, z1, z2, z3, z4);
+                T z1 = v1 + w1, z2 = v2 + w2, z3 = v3 + w3, z4 = -(m1 * v1 + m2 * v2 + m3 * v3) / io.lam;
+                if (!io.plain_nodal) nodal_inverse<T, false>(m1, m2, m3, io.lam, z1, z2, z3, z4, z1, z2, z3, z4);
                 y[j] = (TOut)z1; y[Nn + j] = (TOut)z2; y[2 * Nn + j] = (TOut)z3; y[3 * Nn + j] = (TOut)z4;
             } else if constexpr (OUT == OUT_MATVEC) {
                 const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];

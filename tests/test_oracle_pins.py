@@ -429,6 +429,45 @@ def test_temporal_convergence_printed_errors(scheme, order):
     assert abs(observed - order) <= G["order_tol"], (observed, errs)
 
 
+def comparison_system(N, lam, alpha=0.2, k=1e-2):
+    """The one-step Euler system of Sec. 4.3: m = the manufactured solution at t = 0, right-hand
+    side Chat Lap_N m + (1 + alpha^2)(h + g(t = k)) (oracle arithmetic)."""
+    n = (N, N)
+    g = O.Grid(n, (2 * np.pi, 2 * np.pi))
+    m, _ = I.manufactured2d(n, 0.0, alpha)
+    _, f = I.manufactured2d(n, k, alpha)
+    prm = O.Params(alpha=alpha, k=k, theta=1.0, lam=lam, h_field=f)
+    lap = np.stack([-O.neg_laplacian(g, m[c]) for c in range(3)])
+    b = np.zeros((4,) + g.shape)
+    b[:3] = (1 + alpha ** 2) * lap + (1 + alpha ** 2) * O.h_low(g, prm, m)
+    return g, prm, m, b
+
+
+def test_preconditioner_comparison_counts():
+    """FFT-HSS: 11 GMRES(50) iterations on every 2D grid, no preconditioner: 22 at N = 32
+    (Sec. 4.3); the Sec. 4.4 shift sweep has its minimum, 10 iterations, at lambda = 0.25 on
+    N = 64, 128, 256."""
+    G = GOLD["preconditioner_comparison"]
+    S = GOLD["lambda_sweep"]
+    O.set_transform(O.FFT)
+    try:
+        for pc, key in ((O.PC_FFTHSS, "ffthss"), (O.PC_NONE, "none")):
+            for N, want in zip(G[key]["N"], G[key]["iters"]):
+                g, prm, m, b = comparison_system(N, G["lambda"])
+                _, info = O.gmres_solve(g, prm, O.Opts(restart=G["restart"], rtol=G["rtol"], max_iters=2000,
+                                                       precond=pc), m, b)
+                assert info.converged and info.iters == want, (key, N, info.iters)
+        for N in S["N"]:
+            its = []
+            for lam in S["lambdas"]:
+                g, prm, m, b = comparison_system(N, lam)
+                _, info = O.gmres_solve(g, prm, O.Opts(restart=50, rtol=1e-8, max_iters=2000), m, b)
+                its.append(info.iters)
+            assert min(its) == S["min_iters"] and S["lambdas"][its.index(min(its))] == S["argmin"], (N, its)
+    finally:
+        O.set_transform(O.DFT)
+
+
 # ------------------------------------------------------------------ adjoint vs central finite differences
 
 def test_adjoint_matches_central_differences():
