@@ -184,6 +184,9 @@ def main():
                     help="--apply-sweep with the default launch shapes (for profiling the passes alone)")
     ap.add_argument("--ensemble", action="store_true", help="only the 96-problem batched ensemble (5 Euler steps)")
     ap.add_argument("--adjoint", action="store_true", help="only the 512^2 adjoint timing (16 midpoint steps)")
+    ap.add_argument("--precond-compare", action="store_true",
+                    help="only the comparison of preconditioners and the shift sweep on the one-step Euler "
+                         "system with the manufactured right-hand side (2D)")
     ap.add_argument("--n", type=int, default=128,
                     help="grid points per axis of the midpoint workload (128; smaller only for profiling captures)")
     args = ap.parse_args()
@@ -196,6 +199,8 @@ def main():
         return ensemble_leg(args)
     if args.adjoint:
         return adjoint_leg(args)
+    if args.precond_compare:
+        return precond_compare_leg(args)
 
     import numpy as np
     import torch
@@ -514,6 +519,70 @@ def apply_sweep(args):
         ctx.close()
         del m, p, z
         torch.cuda.empty_cache()
+
+
+def precond_compare_leg(args):
+    """One projected-Euler step (k = 1e-2, alpha = 0.2, GMRES(50), rtol 1e-8) from the
+    manufactured solution at t = 0 with its forcing at t = k, on (0, 2 pi)^2: GMRES iterations
+    and median solve time (3 runs after one warm-up, CUDA events) for the split FFT-HSS, the
+    shifted symmetric part and no preconditioner, N = 32 ... 1024; then the shift sweep
+    lambda = 2^-3 ... 2^4 for N = 64, 128, 256.  The paper's counts and CPU times are quoted
+    as context (its hardware, its SciPy GMRES)."""
+    import numpy as np
+    import torch
+    import paper_2607_15290_b300 as L
+    from paper_2607_15290_b300 import inputs as I
+    alpha, k = 0.2, 1e-2
+    names = {L.PC_FFTHSS: "ffthss", L.PC_HERMITIAN: "symmetric_part", L.PC_NONE: "none"}
+    paper = {"ffthss": {32: 11, 64: 11, 128: 11, 256: 11}, "symmetric_part": {n: 18 for n in (32, 64, 128, 256)},
+             "none": {32: 22, 256: 175}}
+
+    def step(ctx, m, f, lam, pc, reps):
+        prm = L.Params(alpha=alpha, k=k, lam=lam, h_field=f)
+        opts = L.Opts(restart=50, rtol=1e-8, max_iters=20000, preconditioner=pc)
+        times, info = [], None
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(ctx.stream)
+            _, _, info = L.llg_step_euler(ctx, prm, opts, m)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                times.append(e0.elapsed_time(e1))
+        times.sort()
+        return info["iters"], times[len(times) // 2]
+
+    rows = []
+    for N in (32, 64, 128, 256, 512, 1024):
+        n = (N, N)
+        ctx = L.Context(n, (2 * np.pi, 2 * np.pi))
+        m0, _ = I.manufactured2d(n, 0.0, alpha)
+        _, f0 = I.manufactured2d(n, k, alpha)
+        m, f = torch.tensor(m0, device="cuda"), torch.tensor(f0, device="cuda")
+        row = {"N": N}
+        for pc in (L.PC_FFTHSS, L.PC_HERMITIAN, L.PC_NONE):
+            its, ms = step(ctx, m, f, 0.5, pc, 1 if (pc == L.PC_NONE and N >= 512) else 3)
+            row[names[pc]] = {"iters": its, "ms": ms, "paper_iters": paper[names[pc]].get(N)}
+        row["speedup_ffthss_vs_none"] = row["none"]["ms"] / row["ffthss"]["ms"]
+        rows.append(row)
+        ctx.close()
+    sweep = {}
+    lams = [0.125, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0]
+    for N in (64, 128, 256):
+        n = (N, N)
+        ctx = L.Context(n, (2 * np.pi, 2 * np.pi))
+        m0, _ = I.manufactured2d(n, 0.0, alpha)
+        _, f0 = I.manufactured2d(n, k, alpha)
+        m, f = torch.tensor(m0, device="cuda"), torch.tensor(f0, device="cuda")
+        sweep[N] = [step(ctx, m, f, lam, L.PC_FFTHSS, 1)[0] for lam in lams]
+        ctx.close()
+    print(json.dumps({"leg": "precond_compare", "system": "one Euler step, k 1e-2, alpha 0.2, lambda 0.5, GMRES(50), "
+                      "rtol 1e-8, manufactured right-hand side on (0,2pi)^2", "rows": rows,
+                      "lambda_sweep": {"lambdas": lams, "iters": sweep,
+                                       "paper": "minimum 10 at lambda 0.25 on N = 64, 128, 256; 32, 39, 42 at lambda 16"},
+                      "paper_times_s": {"ffthss_256": 0.236, "speedup_vs_none_256": 15.45,
+                                        "hardware": "AMD Ryzen 7 9800X3D, serial SciPy pocketfft"}}), flush=True)
 
 
 def ensemble_leg(args):
