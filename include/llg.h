@@ -70,12 +70,20 @@ typedef struct {
    (DEVICE, 3 FP64 planes, caller-owned, read by the right-hand side and the energy; NULL =
    none).  A time-dependent field (e.g. a manufactured-solution forcing, Sec. 4.2) is passed
    per step, sampled where the scheme samples h_low: t_{n+1} (Euler), t_{n+1/2} (midpoint).
-   The ensemble rejects a non-NULL h_field. */
+   The ensemble rejects a non-NULL h_field.
+   k_an, e_an: uniaxial anisotropy energy k_an (1 - (e_an.m)^2) (field 2 k_an (e_an.m) e_an;
+   e_an a unit vector; k_an = 0: none); demag = 1: the periodic zero-mean demagnetising field
+   h^(xi) = -xi'(xi'.m^)/|xi|^2 (xi' = xi with Nyquist components zeroed), Sec. 2.2, 4.6.
+   Both enter h_low, evaluated at m^n (Euler) or at the Picard midpoint field (midpoint),
+   and the energy; the ensemble and the adjoint reject them. */
 typedef struct {
     double alpha, c_ex, k, theta, lambda;
     double h_ext[3];
     int exchange;
     const double *h_field;
+    double k_an;
+    double e_an[3];
+    int demag;
 } llg_params;
 
 typedef struct {
@@ -190,10 +198,15 @@ llg_status llg_adjoint_step(llg_ctx *ctx, const llg_params *prm, const llg_opts 
                             const double *m_n, const double *x, const double *mbar_next,
                             double *mbar_n, double *dalpha, double dh[3], llg_info *info);
 
-/* Volume-averaged exchange + Zeeman energy g_N(m) = (1/N_g) sum_j [c_ex/2 m.(-Lap_N m) - h.m]
-   (Sec. 2.1; the quadratic-affine energy of Prop. "nodal constraint and energy law").
+/* Volume-averaged energy g_N(m) = (1/N_g) sum_j [c_ex/2 m.(-Lap_N m) - h_j.m
+   + k_an (1 - (e_an.m)^2) - 1/2 m.h_dem] with h_j = h_ext + h_field_j (Sec. 2.1; the
+   quadratic-affine energy of Prop. "nodal constraint and energy law").
    *out is a HOST pointer; synchronises the stream. */
 llg_status llg_energy(llg_ctx *ctx, const llg_params *prm, const double *m, double *out);
+/* Lower-order field h_low(m) = h_ext + h_field + 2 k_an (e_an.m) e_an + h_dem(m) (Sec. 2.1,
+   2.2): the field the steppers add to the exchange term.  m, h: DEVICE, 3 FP64 planes,
+   caller-owned, no aliasing.  Asynchronous on the context stream. */
+llg_status llg_lower_order_field(llg_ctx *ctx, const llg_params *prm, const double *m, double *h);
 
 /* ---------------------------------------------------------------- ensembles
    Many independent 2D problems advanced together by projected-Euler steps (Sec. 2.4, 3.2)

@@ -45,13 +45,19 @@ class Params:
     # optional per-node applied field added to h_ext: CUDA float64 tensor (3, *grid), passed
     # per step (sampled at t_{n+1} for Euler, t_{n+1/2} for the midpoint scheme)
     h_field: object = None
+    # uniaxial anisotropy k_an (1 - (e_an.m)^2) and the periodic demagnetising field (Sec. 4.6)
+    k_an: float = 0.0
+    e_an: tuple = (0.0, 0.0, 1.0)
+    demag: int = 0
 
     def c(self, ctx=None):
         p = _abi.Params()
         p.alpha, p.c_ex, p.k, p.theta, p.lam = self.alpha, self.c_ex, self.k, self.theta, self.lam
         for i in range(3):
             p.h_ext[i] = self.h_ext[i]
+            p.e_an[i] = self.e_an[i]
         p.exchange = self.exchange
+        p.k_an, p.demag = self.k_an, int(self.demag)
         p.h_field = None
         if self.h_field is not None:
             hf = self.h_field
@@ -314,3 +320,10 @@ def llg_energy(ctx: Context, prm: Params, m):
     out = C.c_double(0.0)
     ctx._check(ctx.lib.llg_energy(ctx.h, C.byref(prm.c(ctx)), ctx._arr(m, 3), C.byref(out)))
     return out.value
+
+
+def llg_lower_order_field(ctx: Context, prm: Params, m, out=None):
+    """h_low(m): uniform + per-node applied field, anisotropy and demagnetising fields (3 planes)."""
+    out = out if out is not None else ctx.empty(3)
+    ctx._check(ctx.lib.llg_lower_order_field(ctx.h, C.byref(prm.c(ctx)), ctx._arr(m, 3), ctx._arr(out, 3)))
+    return out

@@ -33,6 +33,7 @@ EXPORTS = [
     "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_ffthss_apply_noalloc",
     "llg_precond_saddle_apply",
     "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy",
+    "llg_lower_order_field",
     "llg_ensemble_create", "llg_ensemble_run", "llg_ensemble_set_blocks", "llg_ensemble_max_blocks",
     "llg_ensemble_autotune", "llg_ensemble_destroy", "llg_ensemble_last_error",
     "llg_autotune", "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate",
@@ -46,7 +47,8 @@ class Grid(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("alpha", C.c_double), ("c_ex", C.c_double), ("k", C.c_double), ("theta", C.c_double),
-                ("lam", C.c_double), ("h_ext", C.c_double * 3), ("exchange", C.c_int), ("h_field", C.c_void_p)]
+                ("lam", C.c_double), ("h_ext", C.c_double * 3), ("exchange", C.c_int), ("h_field", C.c_void_p),
+                ("k_an", C.c_double), ("e_an", C.c_double * 3), ("demag", C.c_int)]
 
 
 class Opts(C.Structure):
@@ -102,6 +104,7 @@ def lib():
     L.llg_step_midpoint.argtypes = [ctx, P(Params), P(Opts), vp, vp, vp, vp, P(Info)]
     L.llg_adjoint_step.argtypes = [ctx, P(Params), P(Opts), vp, vp, vp, vp, d, d, P(Info)]
     L.llg_energy.argtypes = [ctx, P(Params), vp, d]
+    L.llg_lower_order_field.argtypes = [ctx, P(Params), vp, vp]
     L.llg_autotune.argtypes = [ctx, C.c_int, C.c_char_p, C.c_int]
     L.llg_ensemble_create.argtypes = [P(Problem), C.c_int, P(Opts), vp, P(vp)]
     L.llg_ensemble_run.argtypes = [vp, C.c_int, P(Info), P(C.c_int)]

@@ -187,8 +187,11 @@ __global__ void k_mid_final(const double *__restrict__ m, const double *__restri
 }
 
 // energy density sum: m . T - h . m, with T = (c_ex/2)(-Lap) m
+// node sums of c_ex/2 m.(-Lap m) - (h + h_field).m + k_an (1 - (e.m)^2) - 1/2 m.h_dem
+// (T = c_ex/2 (-Lap) m; hf, hd may be NULL)
 __global__ void k_energy_partials(const double *__restrict__ m, const double *__restrict__ T, double h0, double h1,
-                                  double h2, const double *__restrict__ hf, long long N, double *partials) {
+                                  double h2, const double *__restrict__ hf, const double *__restrict__ hd, double kan,
+                                  double e0, double e1, double e2, long long N, double *partials) {
     long long lo, hi;
     block_chunk(N, lo, hi);
     double acc[1] = {0.0};
@@ -200,7 +203,13 @@ __global__ void k_energy_partials(const double *__restrict__ m, const double *__
             g1 += hf[N + j];
             g2 += hf[2 * N + j];
         }
-        acc[0] += a * T[j] + b * T[N + j] + c * T[2 * N + j] - (g0 * a + g1 * b + g2 * c);
+        double ej = a * T[j] + b * T[N + j] + c * T[2 * N + j] - (g0 * a + g1 * b + g2 * c);
+        if (kan != 0.0) {
+            const double em = e0 * a + e1 * b + e2 * c;
+            ej += kan * (1.0 - em * em);
+        }
+        if (hd) ej -= 0.5 * (a * hd[j] + b * hd[N + j] + c * hd[2 * N + j]);
+        acc[0] += ej;
     }
     block_reduce_store<1>(acc, 1, partials + (long long)blockIdx.x * RB_STRIDE);
 }
@@ -263,8 +272,14 @@ llg_status check_params(llg_ctx *c, const llg_params *p) {
         return set_error(c, LLG_ERR_INVALID_ARG, "need alpha > 0, c_ex > 0, lambda > 0, k >= 0, theta > 0");
     if (p->exchange != LLG_EX_SPECTRAL && p->exchange != LLG_EX_FD2)
         return set_error(c, LLG_ERR_INVALID_ARG, "unknown exchange discretisation");
+    if (!std::isfinite(p->k_an) || !std::isfinite(p->e_an[0]) || !std::isfinite(p->e_an[1]) || !std::isfinite(p->e_an[2]))
+        return set_error(c, LLG_ERR_INVALID_ARG, "non-finite anisotropy parameter");
+    if (p->demag != 0 && p->demag != 1) return set_error(c, LLG_ERR_INVALID_ARG, "demag must be 0 or 1");
     return LLG_OK;
 }
+
+// does h_low depend on m (demagnetising or anisotropy field)?
+bool field_depends_on_m(const llg_params *p) { return p->demag != 0 || p->k_an != 0.0; }
 
 llg_status check_opts(llg_ctx *c, const llg_opts *o) {
     if (!o) return set_error(c, LLG_ERR_INVALID_ARG, "opts is NULL");
@@ -423,14 +438,38 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
     return gmres_run(c, ops, flex, o, b, x, info, r0);
 }
 
-llg_status rhs_velocity(llg_ctx *c, const llg_params *p, const double *m, double *b) {
-    // f = Chat Lap_N m + (1 + alpha^2) (h_ext + h_field) ; multiplier row 0
+// the per-node part of h_low(m) (applied field array + demagnetising + anisotropy fields):
+// *hf = NULL when there is none, p->h_field itself when that is all, else `out` (3N)
+llg_status lowfield_nodal(llg_ctx *c, const llg_params *p, const double *m, double *out, const double **hf) {
+    *hf = nullptr;
+    if (!field_depends_on_m(p)) {
+        *hf = p->h_field;
+        return LLG_OK;
+    }
+    const long long N = c->geo.N;
+    llg_status st = LLG_OK;
+    if (p->demag) {
+        if ((st = demag_field(c, m, out)) != LLG_OK) return st;
+    } else {
+        cudaMemsetAsync(out, 0, sizeof(double) * 3 * N, c->stream);
+    }
+    if (p->h_field) {
+        k_axpy3<<<grid_blocks(c), RB_THREADS, 0, c->stream>>>(out, p->h_field, 1.0, out, 3 * N);
+        c->launches++;
+    }
+    if (p->k_an != 0.0 && (st = anisotropy_add(c, m, p->k_an, p->e_an, out)) != LLG_OK) return st;
+    *hf = out;
+    return cuda_check(c, cudaGetLastError(), "lower-order field");
+}
+
+llg_status rhs_velocity(llg_ctx *c, const llg_params *p, const double *m, const double *hf, double *b) {
+    // f = Chat Lap_N m + (1 + alpha^2) (h_ext + per-node part of h_low) ; multiplier row 0
     auto io = make_io<double, double, double>(m, m, b, nullptr, p->lambda);
     const double s = 1.0 + p->alpha * p->alpha;
     io.fld[0] = s * p->h_ext[0];
     io.fld[1] = s * p->h_ext[1];
     io.fld[2] = s * p->h_ext[2];
-    io.hf = p->h_field;
+    io.hf = hf;
     io.hs = s;
     Symbol sym{0.0, -chat(p), 1.0 / (double)c->geo.N, 0, p->exchange};
     return spectral_chain<double, double, double>(c, IN_M, OUT_FIELD, io, sym);
@@ -441,8 +480,15 @@ llg_status energy_async(llg_ctx *c, const llg_params *p, const double *m, double
     Symbol sym{0.0, 0.5 * p->c_ex, 1.0 / (double)c->geo.N, 0, p->exchange};
     llg_status st = spectral_chain<double, double, double>(c, IN_M, OUT_PLAIN, io, sym);
     if (st != LLG_OK) return st;
+    const double *hd = nullptr;
+    if (p->demag) {
+        double *hbuf = c->aux + 21 * c->geo.N;   // 3N scratch no caller of energy_async uses
+        if ((st = demag_field(c, m, hbuf)) != LLG_OK) return st;
+        hd = hbuf;
+    }
     const int nb = reduction_blocks(c);
-    k_energy_partials<<<nb, RB_THREADS, 0, c->stream>>>(m, tmp, p->h_ext[0], p->h_ext[1], p->h_ext[2], p->h_field, c->geo.N, c->red);
+    k_energy_partials<<<nb, RB_THREADS, 0, c->stream>>>(m, tmp, p->h_ext[0], p->h_ext[1], p->h_ext[2], p->h_field, hd,
+                                                        p->k_an, p->e_an[0], p->e_an[1], p->e_an[2], c->geo.N, c->red);
     k_sum_partials_n<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, 1, dst_dev);
     c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "energy");
@@ -545,7 +591,7 @@ llg_status llg_destroy(llg_ctx *c) {
         for (int ex = 0; ex < 2; ++ex) { cudaFree(c->sig64[ex][l]); cudaFree(c->sig32[ex][l]); }
     }
     cudaFree(c->spec64); cudaFree(c->spec32); cudaFree(c->red); cudaFree(c->dsc);
-    cudaFree(c->gdev); cudaFree(c->m32); cudaFree(c->aux);
+    cudaFree(c->gdev); cudaFree(c->m32); cudaFree(c->aux); cudaFree(c->dem_tab);
     for (auto &e : c->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->ghost) cudaFreeHost(c->ghost);
@@ -710,6 +756,29 @@ llg_status llg_energy(llg_ctx *c, const llg_params *p, const double *m, double *
     return LLG_OK;
 }
 
+// h = h_ext + per-node part of h_low(m)
+__global__ void k_add_uniform3(const double *__restrict__ hf, double h0, double h1, double h2, double *h, long long N) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+        h[j] = h0 + (hf ? hf[j] : 0.0);
+        h[N + j] = h1 + (hf ? hf[N + j] : 0.0);
+        h[2 * N + j] = h2 + (hf ? hf[2 * N + j] : 0.0);
+    }
+}
+
+llg_status llg_lower_order_field(llg_ctx *c, const llg_params *p, const double *m, double *h) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st != LLG_OK) return st;
+    if (!m || !h) return set_error(c, LLG_ERR_INVALID_ARG, "null pointer");
+    if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
+    if ((st = ensure_aux(c)) != LLG_OK) return st;
+    const double *hf = nullptr;
+    if ((st = lowfield_nodal(c, p, m, c->aux + 18 * c->geo.N, &hf)) != LLG_OK) return st;
+    k_add_uniform3<<<grid_blocks(c), RB_THREADS, 0, c->stream>>>(hf, p->h_ext[0], p->h_ext[1], p->h_ext[2], h, c->geo.N);
+    c->launches++;
+    return cuda_check(c, cudaGetLastError(), "lower-order field");
+}
+
 llg_status llg_step_euler(llg_ctx *c, const llg_params *p, const llg_opts *o, const double *m_n, double *m_next,
                           double *x_out, llg_info *info) {
     LLG_GUARD(c);
@@ -726,7 +795,9 @@ llg_status llg_step_euler(llg_ctx *c, const llg_params *p, const llg_opts *o, co
     if (o->diagnostics) {
         if ((st = energy_async(c, p, m_n, tmp, c->dsc + 8)) != LLG_OK) return st;
     }
-    if ((st = rhs_velocity(c, p, m_n, b)) != LLG_OK) return st;
+    const double *hf = nullptr;
+    if ((st = lowfield_nodal(c, p, m_n, c->aux + 18 * N, &hf)) != LLG_OK) return st;
+    if ((st = rhs_velocity(c, p, m_n, hf, b)) != LLG_OK) return st;
     cudaMemsetAsync(x_out, 0, sizeof(double) * 4 * N, c->stream);
     st = solve(c, p, 1.0, o, m_n, b, x_out, &inf);
     if (st != LLG_OK && st != LLG_ERR_NOT_CONVERGED) { inf.status = st; if (info) *info = inf; return st; }
@@ -771,8 +842,13 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
     if (o->diagnostics) {
         if ((st = energy_async(c, p, m_n, tmp, c->dsc + 8)) != LLG_OK) return st;
     }
-    if ((st = rhs_velocity(c, p, m_n, b)) != LLG_OK) return st;
+    // exchange at m^n, lower-order field at the midpoint field mhat (eq. (hatm))
+    const bool mdep = field_depends_on_m(p);
+    double *hfbuf = c->aux + 18 * N;   // 3N
+    const double *hf = nullptr;
     k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, v_prev, 0.5 * p->k, mhat, 3 * N);
+    if ((st = lowfield_nodal(c, p, mhat, hfbuf, &hf)) != LLG_OK) return st;
+    if ((st = rhs_velocity(c, p, m_n, hf, b)) != LLG_OK) return st;
     // warm start (v_prev | 0), or zero
     if (v_prev) cudaMemcpyAsync(x_out, v_prev, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
     else cudaMemsetAsync(x_out, 0, sizeof(double) * 3 * N, c->stream);
@@ -799,6 +875,15 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
             if (std::sqrt(c->hsc[0]) <= o->picard_tol * std::sqrt(c->hsc[1])) { conv = true; break; }
         }
         cudaMemcpyAsync(vold, x_out, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
+        if (mdep) {
+            // the right-hand side moves with mhat: rebuild it, solve from the true residual
+            k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, 3 * N);
+            c->launches++;
+            if ((st = lowfield_nodal(c, p, mhat, hfbuf, &hf)) != LLG_OK) return st;
+            if ((st = rhs_velocity(c, p, m_n, hf, b)) != LLG_OK) return st;
+            have_r0 = false;
+            continue;
+        }
         if (c->ws.last_res) {
             k_picard_advance<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, c->ws.last_res, r0, N);
             have_r0 = true;
@@ -838,6 +923,8 @@ llg_status llg_adjoint_step(llg_ctx *c, const llg_params *p, const llg_opts *o, 
     if (st == LLG_OK) st = check_opts(c, o);
     if (st != LLG_OK) return st;
     if (!m_n || !x || !mbar_next || !mbar_n || !dalpha || !dh) return set_error(c, LLG_ERR_INVALID_ARG, "null pointer");
+    if (field_depends_on_m(p))
+        return set_error(c, LLG_ERR_INVALID_ARG, "the adjoint covers exchange and applied fields (no demag or anisotropy)");
     if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
     if ((st = ensure_aux(c)) != LLG_OK) return st;
     const long long N = c->geo.N;

@@ -841,7 +841,8 @@ llg_status llg_ensemble_create(const llg_problem *probs, int count, const llg_op
         if (!(p.alpha > 0) || !(p.c_ex > 0) || !(p.lambda > 0) || p.k < 0 || !(q.L[0] > 0) || !(q.L[1] > 0))
             return fail(LLG_ERR_INVALID_ARG, "params");
         if (p.exchange != LLG_EX_SPECTRAL && p.exchange != LLG_EX_FD2) return fail(LLG_ERR_INVALID_ARG, "exchange");
-        if (p.h_field) return fail(LLG_ERR_INVALID_ARG, "per-node applied fields are not supported in ensembles");
+        if (p.h_field || p.demag || p.k_an != 0.0)
+            return fail(LLG_ERR_INVALID_ARG, "ensembles take exchange and uniform applied fields only");
         std::vector<double> key = {(double)q.n[0], (double)q.n[1], q.L[0], q.L[1], (double)p.exchange};
         auto it = key_to_cls.find(key);
         if (it == key_to_cls.end()) {

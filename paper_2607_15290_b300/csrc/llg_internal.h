@@ -125,6 +125,7 @@ struct llg_ctx {
     size_t prof_used = 0;
     int prof_open = -1;
     std::vector<std::pair<const void *, int>> occ;   // grid size per Arnoldi kernel (one full wave)
+    double *dem_tab = nullptr;   // demagnetising wavevector tables (xi, xi' per axis)
 };
 
 namespace llg {
@@ -141,6 +142,13 @@ void prof_discard(llg_ctx *c, size_t first, int min_tag);
 
 // spectral.cu
 llg_status autotune(llg_ctx *c, int prec_mask, std::string *report);
+// FP64 Fourier transform along axis 1 (3D y) of every spectral column, no multiplier
+llg_status plain_axis_pass64(llg_ctx *c, int axis, bool forward);
+
+// demag.cu: h = periodic zero-mean demagnetising field of m (3 planes, FP64; uses the FP64
+// spectral buffer); h += 2 k_an (e . m) e
+llg_status demag_field(llg_ctx *c, const double *m, double *h);
+llg_status anisotropy_add(llg_ctx *c, const double *m, double kan, const double e_an[3], double *h);
 template <typename T, typename TIn, typename TOut>
 llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<TIn, TOut, T> &io,
                           const Symbol &sym);

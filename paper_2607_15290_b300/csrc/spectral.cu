@@ -293,6 +293,19 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
     return LLG_OK;
 }
 
+llg_status plain_axis_pass64(llg_ctx *c, int axis, bool forward) {
+    if (axis != 1 || c->geo.dim != 3) return set_error(c, LLG_ERR_INVALID_ARG, "plain axis pass: 3D y axis only");
+    ColArgs<double> ca;
+    int batches = 1, mode = 1;
+    Symbol sym{1.0, 0.0, 1.0, 0, 0};
+    slot_args<double>(c, forward ? SLOT_Y_FWD : SLOT_Y_INV, sym, ca, batches, mode);
+    // the register kernel covers every column slot (the staged one only the live ones of
+    // the packed layout)
+    const cudaError_t e = launch_col_cfg<double>(c, mode, ca, batches, col_default<double>(ca.nl));
+    c->launches++;
+    return cuda_check(c, e, "axis pass");
+}
+
 // ------------------------------------------------------------------ autotuner
 
 // deterministic pseudo-random fill in [-1, 1) (hash of the index)
