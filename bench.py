@@ -187,6 +187,8 @@ def main():
     ap.add_argument("--precond-compare", action="store_true",
                     help="only the comparison of preconditioners and the shift sweep on the one-step Euler "
                          "system with the manufactured right-hand side (2D)")
+    ap.add_argument("--mesh-study", action="store_true",
+                    help="only the random right-hand-side mesh study (fixed k vs bounded stiffness, 2D)")
     ap.add_argument("--n", type=int, default=128,
                     help="grid points per axis of the midpoint workload (128; smaller only for profiling captures)")
     args = ap.parse_args()
@@ -201,6 +203,8 @@ def main():
         return adjoint_leg(args)
     if args.precond_compare:
         return precond_compare_leg(args)
+    if args.mesh_study:
+        return mesh_study_leg(args)
 
     import numpy as np
     import torch
@@ -583,6 +587,46 @@ def precond_compare_leg(args):
                                        "paper": "minimum 10 at lambda 0.25 on N = 64, 128, 256; 32, 39, 42 at lambda 16"},
                       "paper_times_s": {"ffthss_256": 0.236, "speedup_vs_none_256": 15.45,
                                         "hardware": "AMD Ryzen 7 9800X3D, serial SciPy pocketfft"}}), flush=True)
+
+
+def mesh_study_leg(args):
+    """Sec. 4.5's mesh study on the GPU: the velocity right-hand side replaced by three seeded
+    normalised Gaussian vectors (seeds 20260724-26; not the paper's NumPy vectors), multiplier
+    part zero, FFT-HSS GMRES(50) in FP64 at rtol 1e-8, the Sec. 4.3 field; fixed k = 1e-2 and
+    bounded stiffness kN^2 = 10.24, N = 32 ... 1024.  Median/min/max iterations and median
+    solve time; the paper's medians quoted as context."""
+    import numpy as np
+    import torch
+    import paper_2607_15290_b300 as L
+    from paper_2607_15290_b300 import inputs as I
+    paper = {"fixed": {32: 55, 256: 608}, "bounded": {32: 55, 256: 56}}
+    rows = []
+    for regime in ("fixed", "bounded"):
+        for N in (32, 64, 128, 256, 512, 1024):
+            k = 1e-2 if regime == "fixed" else 10.24 / N ** 2
+            n = (N, N)
+            ctx = L.Context(n, (2 * np.pi, 2 * np.pi))
+            m0, _ = I.manufactured2d(n, 0.0, 0.2)
+            m = torch.tensor(m0, device="cuda")
+            prm = L.Params(alpha=0.2, k=k, theta=1.0, lam=0.5)
+            opts = L.Opts(restart=50, rtol=1e-8, max_iters=20000)
+            its, times, worst = [], [], 0.0
+            for seed in (20260724, 20260725, 20260726):
+                b = torch.tensor(I.gaussian_rhs(n, seed), device="cuda")
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(ctx.stream)
+                _, info = L.llg_gmres_solve(ctx, prm, opts, m, b)
+                e1.record(ctx.stream)
+                torch.cuda.synchronize()
+                its.append(info["iters"])
+                times.append(e0.elapsed_time(e1))
+                worst = max(worst, info["rel_res_true"])
+            ctx.close()
+            rows.append({"regime": regime, "N": N, "k": k, "iters_median": sorted(its)[1], "iters_min": min(its),
+                         "iters_max": max(its), "ms_median": sorted(times)[1], "worst_rel_res": worst,
+                         "paper_median": paper[regime].get(N)})
+    print(json.dumps({"leg": "mesh_study", "rows": rows}), flush=True)
 
 
 def ensemble_leg(args):
