@@ -126,6 +126,78 @@ __device__ __forceinline__ void fft(C (&a)[E], C *buf0, C *buf1, int t, const C 
     stage<LOGN, E, SIGN, L, 0, PAR, DB>(a, buf0, buf1, t, tw);
 }
 
+// ---------------------------------------------------------------- two adjacent FP32 lines
+
+// The same stages for two FP32 lines held by one thread (columns cc and cc + 1 of a
+// column tile, ColL layout with even stride SS): every shared-memory access moves both
+// lines' elements as one 16-byte word and each twiddle serves both lines.
+__device__ __forceinline__ float4 pack2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+template <int LOGN, int E, int SIGN, int SS, int S, int PAR, bool DB>
+__device__ __forceinline__ void stage2(float2 (&a)[E], float2 (&b)[E], float2 *buf0, float2 *buf1, int t,
+                                       const float2 *__restrict__ tw) {
+    using PL = Plan<LOGN, E>;
+    constexpr int R = 1 << PL::lr(S), Ns = PL::Ns(S), Q = E / R, P = PL::P, N = PL::N;
+    constexpr bool last = S == PL::NST - 1;
+    constexpr int TWS = N / (R * Ns);
+    if constexpr (S > 0) {
+        __syncthreads();
+        const float2 *src = ((S - 1 + PAR) & 1) ? buf1 : buf0;
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            const float4 x = *reinterpret_cast<const float4 *>(&src[(t + P * s) * SS]);
+            a[s] = make_float2(x.x, x.y);
+            b[s] = make_float2(x.z, x.w);
+        }
+    }
+    if constexpr (!DB && !last) __syncthreads();
+    float2 *dst = ((S + PAR) & 1) ? buf1 : buf0;
+    int kt = 0, b0 = 0;
+    if constexpr (Ns <= P) {
+        kt = t & (Ns - 1);
+        b0 = R * (t - kt) + kt;
+    } else {
+        b0 = t;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        float2 u[R], w[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { u[r] = a[q + r * Q]; w[r] = b[q + r * Q]; }
+        if constexpr (Ns > 1) {
+            int k;
+            if constexpr (Ns <= P) k = kt;
+            else k = t + P * (q % (Ns / P));
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const float2 f = tw_load<SIGN>(tw, r * k * TWS);
+                u[r] = cmul(u[r], f);
+                w[r] = cmul(w[r], f);
+            }
+        }
+        if constexpr (R == 2) { dft2<SIGN>(u[0], u[1]); dft2<SIGN>(w[0], w[1]); }
+        else if constexpr (R == 4) { dft4<SIGN>(u[0], u[1], u[2], u[3]); dft4<SIGN>(w[0], w[1], w[2], w[3]); }
+        else { dft8<SIGN>(u); dft8<SIGN>(w); }
+        if constexpr (last) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) { a[q + r * Q] = u[r]; b[q + r * Q] = w[r]; }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int c0 = Ns <= P ? R * P * q + r * Ns : R * Ns * (q / (Ns / P)) + P * (q % (Ns / P)) + r * Ns;
+                *reinterpret_cast<float4 *>(&dst[(b0 + c0) * SS]) = pack2(u[r], w[r]);
+            }
+        }
+    }
+    if constexpr (!last) stage2<LOGN, E, SIGN, SS, S + 1, PAR, DB>(a, b, buf0, buf1, t, tw);
+}
+
+template <int LOGN, int E, int SIGN, int SS, int PAR = 0, bool DB = true>
+__device__ __forceinline__ void fft2(float2 (&a)[E], float2 (&b)[E], float2 *buf0, float2 *buf1, int t,
+                                     const float2 *__restrict__ tw) {
+    stage2<LOGN, E, SIGN, SS, 0, PAR, DB>(a, b, buf0, buf1, t, tw);
+}
+
 // the buffer that no stage of a transform with parity PAR reads last, free for the
 // caller right after the transform returns
 template <int LOGN, int E, int PAR>

@@ -83,7 +83,8 @@ struct GmresDev;   // device-side Arnoldi state (krylov.cu)
 
 // launch shape of an axis pass: kind 0 = register kernel (E elements per thread, TW
 // columns per block); kind 1 = staged kernel (TW = tile columns, CB = columns per
-// compute sub-batch, E = 8)
+// compute sub-batch, E = 8); kind 3 = FP32 register kernel with two adjacent columns
+// per thread (16-byte accesses; TW columns per tile)
 struct ColCfg {
     int kind, E, TW, CB;
 };

@@ -122,6 +122,7 @@ static cudaError_t launch_staged(llg_ctx *c, int mode, const ColArgs<float> &a, 
     return cudaErrorInvalidValue;
 }
 
+static int ilog2_int(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 template <typename T> static int col_E(int nl) { return (sizeof(T) == 4 && nl >= 1024) ? 16 : (nl >= 8 ? 8 : nl); }
 
 // every launch shape the tuner may pick for a line length
@@ -135,6 +136,11 @@ template <typename T> static std::vector<ColCfg> col_candidates(int nl) {
         if (TW * (nl / E) > 512) continue;
         if ((size_t)nl * TW * sizeof(cplx<T>) > 200 * 1024) continue;
         v.push_back({0, E, TW, 0});
+    }
+    if (sizeof(T) == 4 && ct::covers(ilog2_int(nl))) {
+        // two adjacent columns per thread (16-byte accesses)
+        for (int TW : {8, 16})
+            if ((TW / 2) * (nl / E) <= 512) v.push_back({3, E, TW, 0});
     }
     if (sizeof(T) == 4 && nl >= 64) {
         for (auto &sc : kStaged) {
@@ -164,6 +170,12 @@ static cudaError_t launch_col_cfg(llg_ctx *c, int mode, const ColArgs<T> &a, int
         return cudaErrorInvalidValue;
     }
     const dim3 grid(a.S / cfg.TW, batches);
+    if (cfg.kind == 3) {
+        if constexpr (sizeof(T) == 4) {
+            if (ct::covers(a.logn)) return ct::col_v2(c, a.logn, mode, a, grid, cfg.TW);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (ct::covers(a.logn) && cfg.E == col_E<T>(a.nl)) return ct::col<T>(c, a.logn, mode, a, grid, cfg.TW);
 #define LLG_CE(EE, TT) if (cfg.E == EE && cfg.TW == TT) return launch_col_ETW<T, EE, TT>(c, mode, a, grid);
     if constexpr (sizeof(T) == 8) {
@@ -344,6 +356,7 @@ __global__ void k_live_maxdiff(const C *a, const C *b, long long rows, int S, in
 static std::string cfg_name(const ColCfg &f) {
     char b[64];
     if (f.kind == 0) snprintf(b, sizeof b, "register(E%d,TW%d)", f.E, f.TW);
+    else if (f.kind == 3) snprintf(b, sizeof b, "paired(E%d,TW%d)", f.E, f.TW);
     else snprintf(b, sizeof b, "staged(TW%d,CB%d)", f.TW, f.CB);
     return b;
 }

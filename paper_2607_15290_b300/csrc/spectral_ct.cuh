@@ -351,6 +351,39 @@ __global__ void __launch_bounds__(TW *((1 << LOGN) / E), (sizeof(T) == 4 && TW *
     col_ct_body<T, LOGN, E, TW, MODE, DB>(a, blockIdx.x, blockIdx.y, smraw);
 }
 
+// FP32 axis pass with two adjacent columns per thread (TW columns per tile, TW/2 threads
+// per tile row): global loads/stores and every shared-memory exchange are 16-byte words.
+template <int LOGN, int TW, int MODE, bool DB>
+__global__ void __launch_bounds__((TW / 2) * ((1 << LOGN) / LineE<float, LOGN>::value), 2) col_ct_v2(ColArgs<float> a) {
+    using C = float2;
+    constexpr int N = 1 << LOGN, E = LineE<float, LOGN>::value, P = N / E;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *buf0 = reinterpret_cast<C *>(smraw);
+    C *buf1 = DB ? buf0 + N * TW : buf0;
+    const int c2 = 2 * (threadIdx.x % (TW / 2)), t = threadIdx.x / (TW / 2);
+    const int col = blockIdx.x * TW + c2, by = blockIdx.y;
+    C *p = a.spec + (long long)by * a.bs + col + (long long)t * a.ls;
+    const long long step = (long long)P * a.ls;
+    C v[E], w[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const float4 x = *reinterpret_cast<const float4 *>(&p[q * step]);
+        v[q] = make_float2(x.x, x.y);
+        w[q] = make_float2(x.z, x.w);
+    }
+    if constexpr ((MODE & 1) != 0) fft2<LOGN, E, -1, TW, 0, DB>(v, w, buf0 + c2, buf1 + c2, t, a.tw);
+    if constexpr ((MODE & 4) != 0) {
+        apply_symbol<float, LOGN, E, ColL<TW>>(v, a, col, by, t);
+        apply_symbol<float, LOGN, E, ColL<TW>>(w, a, col + 1, by, t);
+    }
+    if constexpr ((MODE & 2) != 0) {
+        constexpr int PAR = (MODE & 1) ? FreeBuf<LOGN, E, 0>::value : 0;
+        fft2<LOGN, E, +1, TW, PAR, DB>(v, w, buf0 + c2, buf1 + c2, t, a.tw);
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) *reinterpret_cast<float4 *>(&p[q * step]) = pack2(v[q], w[q]);
+}
+
 // staged FP32 axis pass (see col_staged_kernel): the whole tile of TWL columns is
 // copied to shared memory with 16-byte asynchronous copies; CB columns at a time are
 // transformed in place in the tile (single exchange buffer: the column itself).

@@ -1,6 +1,7 @@
 // spectral_ct_inst.cuh -- definitions and explicit instantiations of the
 // compile-time-length launchers for one LOGN (set by the including file).
 #pragma once
+#include <algorithm>
 #include "spectral_ct.cuh"
 #include "spectral_ct_launch.h"
 
@@ -96,6 +97,37 @@ cudaError_t col_launch(llg_ctx *c, int mode, const ColArgs<T> &a, dim3 grid, int
     return cudaErrorInvalidValue;
 }
 
+template <int LOGN, int TW>
+static cudaError_t col_v2_launch_tw(llg_ctx *c, int mode, const ColArgs<float> &a, dim3 grid) {
+    constexpr int N = 1 << LOGN, E = LineE<float, LOGN>::value, threads = (TW / 2) * (N / E);
+    if constexpr (threads > 512 || threads < 32) {
+        return cudaErrorInvalidValue;
+    } else {
+        constexpr bool DB = 2 * N * TW * sizeof(float2) <= 96 * 1024;
+        constexpr size_t sm = (DB ? 2 : 1) * (size_t)N * TW * sizeof(float2);
+#define LLG_C2(MODE)                                                   \
+    case MODE: {                                                       \
+        auto k = col_ct_v2<LOGN, TW, MODE, DB>;                        \
+        cudaError_t e = prep(k);                                       \
+        if (e != cudaSuccess) return e;                                \
+        k<<<grid, threads, sm, c->stream>>>(a);                        \
+        return cudaGetLastError();                                     \
+    }
+        switch (mode) {
+            LLG_C2(1) LLG_C2(2) LLG_C2(7)
+        }
+#undef LLG_C2
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <int LOGN>
+cudaError_t col_v2_launch(llg_ctx *c, int mode, const ColArgs<float> &a, dim3 grid, int TW) {
+    if (TW == 16) return col_v2_launch_tw<LOGN, 16>(c, mode, a, grid);
+    if (TW == 8) return col_v2_launch_tw<LOGN, 8>(c, mode, a, grid);
+    return cudaErrorInvalidValue;
+}
+
 template <int LOGN, int TWL, int CB>
 static cudaError_t staged_launch_tw(llg_ctx *c, int mode, const ColArgs<float> &a, int live, int batches) {
     constexpr int N = 1 << LOGN, threads = CB * (N / 8);
@@ -141,6 +173,7 @@ LLG_CT_ROWS(float, float, float)
 template cudaError_t col_launch<double, LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<double> &, dim3, int);
 template cudaError_t col_launch<float, LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<float> &, dim3, int);
 template cudaError_t staged_launch<LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<float> &, int, int, int, int);
+template cudaError_t col_v2_launch<LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<float> &, dim3, int);
 
 }  // namespace ct
 }  // namespace llg

@@ -18,6 +18,8 @@ template <typename T, int LOGN>
 cudaError_t col_launch(llg_ctx *c, int mode, const ColArgs<T> &a, dim3 grid, int TW);
 template <int LOGN>
 cudaError_t staged_launch(llg_ctx *c, int mode, const ColArgs<float> &a, int live, int batches, int TWL, int CB);
+template <int LOGN>
+cudaError_t col_v2_launch(llg_ctx *c, int mode, const ColArgs<float> &a, dim3 grid, int TW);
 
 // shared memory of a row block of G pairs: two exchange buffers of 3G padded lines
 template <typename T> inline size_t row_smem(int n0, int G) { return (size_t)2 * 3 * G * (n0 + n0 / 8) * sizeof(cplx<T>); }
@@ -52,6 +54,9 @@ inline cudaError_t col(llg_ctx *c, int logn, int mode, const ColArgs<T> &a, dim3
 }
 inline cudaError_t staged(llg_ctx *c, int logn, int mode, const ColArgs<float> &a, int live, int batches, int TWL, int CB) {
     LLG_CT_SWITCH(logn, (staged_launch<LG>(c, mode, a, live, batches, TWL, CB)))
+}
+inline cudaError_t col_v2(llg_ctx *c, int logn, int mode, const ColArgs<float> &a, dim3 grid, int TW) {
+    LLG_CT_SWITCH(logn, (col_v2_launch<LG>(c, mode, a, grid, TW)))
 }
 #undef LLG_CT_SWITCH
 #endif
