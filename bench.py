@@ -56,6 +56,22 @@ ARNOLDI_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averag
                         "arnoldi_pass launches of this workload (exact-count kernels, fused reduction)")
 
 
+def aggregate_over_ranks(dist, ms, counts, device):
+    """Whole-job figures of N independent replicas: the timed region lasts as long as the
+    slowest rank (MAX over ranks of the per-rank CUDA-event time), the work done is the SUM
+    over ranks of each counter.  dist is torch.distributed (or None for one rank); device
+    holds the reduction tensors ("cuda" for NCCL, "cpu" for gloo)."""
+    if dist is None:
+        return float(ms), {k: float(v) for k, v in counts.items()}
+    import torch
+    keys = sorted(counts)
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(counts[k]) for k in keys], device=device, dtype=torch.float64)
+    dist.all_reduce(c)
+    return float(t.item()), {k: float(v) for k, v in zip(keys, c.tolist())}
+
+
 def workload_params(n=128):
     import numpy as np
     alpha = 0.1
@@ -271,16 +287,9 @@ def main():
     clk = clocks.stop()
     gpu_launches = ctx.launches() - l0
     ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        a = torch.tensor([applies], device="cuda", dtype=torch.float64)
-        dist.all_reduce(a)
-        applies_total = float(a.item())
-    else:
-        applies_total = applies
-    value = applies_total / (ms / 1e3)
+    ms, totals = aggregate_over_ranks(dist, ms, {"applies": applies, "solves": solves, "steps": args.steps},
+                                      "cuda")
+    value = totals["applies"] / (ms / 1e3)
 
     extras = {}
     pk = peaks()
@@ -316,7 +325,7 @@ def main():
                    "restart": 30, "rtol": 1e-10, "picard_tol": 1e-10,
                    "l2": "inputs larger than L2 (fields 50-67 MB each, Krylov basis ~2 GB)",
                    "parallelism": f"replicas x{world} (independent problems, no collective)"},
-        "solves_per_s": solves * world / (ms / 1e3), "steps_per_s": args.steps * world / (ms / 1e3),
+        "solves_per_s": totals["solves"] / (ms / 1e3), "steps_per_s": totals["steps"] / (ms / 1e3),
         "gmres_iters_per_solve": iters / max(solves, 1), "max_len_drift": drift,
         "roofline": roof, "gpu_launches": gpu_launches, "clocks": clk,
         "fp64_fma_tflops_measured": fp64_peak, "fp32_fma_tflops_measured": fp32_peak,
