@@ -78,7 +78,7 @@ def test_full_size_apply_and_matvec(oracle_fft, n):
     ctx.close()
 
 
-def test_full_size_256cube_fp32_apply(oracle_fft):
+def test_full_size_256cube_apply(oracle_fft):
     n = (256, 256, 256)
     og = O.Grid(n)
     ctx = L.Context(n)
@@ -91,6 +91,10 @@ def test_full_size_256cube_fp32_apply(oracle_fft):
     ref = O.ffthss_apply(og, po, m, p)
     got = host(L.llg_ffthss_apply_f32(ctx, pl, gpu(m, torch.float32), gpu(p, torch.float32)))
     assert rel(got, ref) <= 2e-5
+    # FP64 apply and saddle matvec at the full 256^3 size as well
+    gm, gp = gpu(m), gpu(p)
+    assert rel(host(L.llg_ffthss_apply(ctx, pl, gm, gp)), ref) <= 1e-12
+    assert rel(host(L.llg_saddle_apply(ctx, pl, gm, gp)), O.saddle_apply(og, po, m, p)) <= 1e-12
     ctx.close()
 
 
