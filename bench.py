@@ -205,6 +205,9 @@ def main():
                          "system with the manufactured right-hand side (2D)")
     ap.add_argument("--mesh-study", action="store_true",
                     help="only the random right-hand-side mesh study (fixed k vs bounded stiffness, 2D)")
+    ap.add_argument("--midpoint-2d", action="store_true",
+                    help="only the 1024^2 FP64 midpoint workload (20 steps, smooth and broadband fields): "
+                         "iterations per solve, nodal drift, dissipation residual")
     ap.add_argument("--n", type=int, default=128,
                     help="grid points per axis of the midpoint workload (128; smaller only for profiling captures)")
     args = ap.parse_args()
@@ -221,6 +224,8 @@ def main():
         return precond_compare_leg(args)
     if args.mesh_study:
         return mesh_study_leg(args)
+    if args.midpoint_2d:
+        return midpoint_2d_leg(args)
 
     import numpy as np
     import torch
@@ -596,6 +601,51 @@ def precond_compare_leg(args):
                                        "paper": "minimum 10 at lambda 0.25 on N = 64, 128, 256; 32, 39, 42 at lambda 16"},
                       "paper_times_s": {"ffthss_256": 0.236, "speedup_vs_none_256": 15.45,
                                         "hardware": "AMD Ryzen 7 9800X3D, serial SciPy pocketfft"}}), flush=True)
+
+
+def midpoint_2d_leg(args):
+    """1024^2 periodic unit square, FP64 throughout, alpha = 0.02, midpoint scheme for 20 steps
+    at 13.3x the linearised explicit exchange limit (Picard and GMRES(30) tolerances 1e-10),
+    for the smooth field and the broadband field (|k|^-1.5 spectrum, seeded): GMRES
+    iterations per linear solve, Picard iterations per step, worst nodal length drift, worst
+    discrete dissipation residual, and step time (CUDA events, after one warm-up step)."""
+    import numpy as np
+    import torch
+    import paper_2607_15290_b300 as L
+    from paper_2607_15290_b300 import inputs as I
+    n = (1024, 1024)
+    alpha = 0.02
+    k = 13.3 * 2 * alpha / ((1 + alpha ** 2) * 2 * (math.pi * n[0]) ** 2)
+    ctx = L.Context(n)
+    ctx.autotune(fp64=True, fp32=False)
+    prm = L.Params(alpha=alpha, k=k, theta=0.5, lam=0.5)
+    opts = L.Opts(restart=30, rtol=1e-10, picard_tol=1e-10, picard_max=60, diagnostics=1)
+    out = {"leg": "midpoint_2d", "grid": list(n), "alpha": alpha, "dt": k, "dt_over_explicit_limit": 13.3, "fields": {}}
+    for field in ("smooth", "broadband"):
+        m0 = I.smooth2d(n) if field == "smooth" else I.broadband(n, seed=20260725)
+        m = torch.tensor(m0, device="cuda")
+        L.llg_step_midpoint(ctx, prm, opts, m, None)      # warm-up
+        vprev = None
+        iters = solves = 0
+        drift = diss = 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        for _ in range(20):
+            m, x, info = L.llg_step_midpoint(ctx, prm, opts, m, vprev)
+            vprev = x[:3].contiguous()
+            iters += info["iters"]
+            solves += info["picard_iters"]
+            drift = max(drift, info["max_len_drift"])
+            diss = max(diss, abs(info["dissipation_residual"]) / max(abs(info["energy_before"]), 1e-300))
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        out["fields"][field] = {"gmres_iters_per_solve": iters / solves, "picard_iters_per_step": solves / 20,
+                                "max_len_drift": drift, "max_rel_dissipation_residual": diss,
+                                "ms_per_step": ms, "steps_per_s": 1e3 / ms}
+    ctx.close()
+    print(json.dumps(out), flush=True)
 
 
 def mesh_study_leg(args):
