@@ -349,9 +349,10 @@ Symbol sym_forward(llg_ctx *c, const llg_params *p, double theta) {
 // FP64 operators ------------------------------------------------------------
 
 llg_status op_matvec64(llg_ctx *c, const llg_params *p, double theta, const double *m, const double *x,
-                       const double *scale, double *y, int transpose) {
+                       const double *scale, double *y, int transpose, const int *skip = nullptr) {
     auto io = make_io<double, double, double>(m, x, y, scale, p->lambda);
     io.transpose = transpose;
+    io.skip = skip;
     return spectral_chain<double, double, double>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
 }
 
@@ -363,9 +364,10 @@ llg_status op_apply64(llg_ctx *c, const llg_params *p, double theta, const doubl
 }
 
 llg_status op_fused64(llg_ctx *c, const llg_params *p, double theta, const double *m, const double *x,
-                      const double *scale, double *y, int plain_nodal = 0) {
+                      const double *scale, double *y, int plain_nodal = 0, const int *skip = nullptr) {
     auto io = make_io<double, double, double>(m, x, y, scale, p->lambda);
     io.plain_nodal = plain_nodal;
+    io.skip = skip;
     return spectral_chain<double, double, double>(c, IN_FUSED, OUT_FUSED, io, sym_shifted_inverse(c, p, theta));
 }
 
@@ -408,16 +410,20 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
     SolveOps ops;
     ops.matvec = [=](const double *xx, double *yy) { return op_matvec64(c, p, theta, m, xx, nullptr, yy, 0); };
     const int pc = o->preconditioner;
+    // operators issued inside a GMRES cycle return at once once the cycle's stopping flag
+    // is set (the host polls it only every few iterations); v_0 and the true residual,
+    // issued outside cycles, always run
+    const int *cyc = &c->gdev->done;
     if (!flex) {
         if (pc == LLG_PC_NONE) {
             ops.prec = [=](const double *xx, const double *s, double *yy) { return op_scaled_copy<double>(c, xx, s, yy); };
-            ops.pop = [=](const double *xx, const double *s, double *yy) { return op_matvec64(c, p, theta, m, xx, s, yy, 0); };
+            ops.pop = [=](const double *xx, const double *s, double *yy) { return op_matvec64(c, p, theta, m, xx, s, yy, 0, cyc); };
         } else if (pc == LLG_PC_HERMITIAN) {
             ops.prec = [=](const double *xx, const double *s, double *yy) { return op_hermitian64(c, p, theta, m, xx, s, yy); };
-            ops.pop = [=](const double *xx, const double *s, double *yy) { return op_fused64(c, p, theta, m, xx, s, yy, 1); };
+            ops.pop = [=](const double *xx, const double *s, double *yy) { return op_fused64(c, p, theta, m, xx, s, yy, 1, cyc); };
         } else {
             ops.prec = [=](const double *xx, const double *s, double *yy) { return op_apply64(c, p, theta, m, xx, s, yy, 0); };
-            ops.pop = [=](const double *xx, const double *s, double *yy) { return op_fused64(c, p, theta, m, xx, s, yy); };
+            ops.pop = [=](const double *xx, const double *s, double *yy) { return op_fused64(c, p, theta, m, xx, s, yy, 0, cyc); };
         }
     } else {
         if ((st = ensure_m32(c)) != LLG_OK) return st;
@@ -428,10 +434,12 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
             if (pc == LLG_PC_NONE) return op_scaled_copy<float>(c, xx, s, zz);
             auto io = make_io<double, float, float>(m32, xx, zz, s, p->lambda);
             io.plain_nodal = pc == LLG_PC_HERMITIAN;
+            io.skip = cyc;
             return spectral_chain<float, double, float>(c, IN_V, OUT_APPLY, io, sym_shifted_inverse(c, p, theta));
         };
         ops.fmatvec = [=](const float *zz, double *ww) {
             auto io = make_io<float, double, float>(m32, zz, ww, nullptr, p->lambda);
+            io.skip = cyc;
             return spectral_chain<float, float, double>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
         };
     }

@@ -223,7 +223,7 @@ __device__ __forceinline__ RowArgs<T, TIn, TOut> row_args(const EnsProb &P, cons
 
 template <typename T>
 __device__ __forceinline__ ColArgs<T> col_args(const EnsProb &P, const EnsClass &C, double sa, double sb, int inv) {
-    ColArgs<T> c;
+    ColArgs<T> c{};
     c.spec = spec_of<T>(P);
     c.tw = tw_of<T>(C, 1);
     c.ls = C.S; c.bs = 0;

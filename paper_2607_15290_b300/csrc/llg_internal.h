@@ -66,6 +66,9 @@ struct NodalIO {
     // OUT_FIELD only: optional per-node field added as hs * hf (3 FP64 planes)
     const double *hf;
     double hs;
+    // optional device flag: when set, every pass of the chain returns at once (operators
+    // queued inside a GMRES cycle that has already converged)
+    const int *skip;
 };
 
 struct Workspace {

@@ -186,7 +186,7 @@ extern "C" llg_status llg_ffthss_apply_noalloc(const llg_grid *grid, const llg_p
     ra.io.m = m; ra.io.x = p; ra.io.y = z; ra.io.scale = nullptr; ra.io.lam = prm->lambda;
 
     // axis passes with the shifted exchange symbol 1 / (alpha + lambda + theta k Chat sigma), 1/N_g folded in
-    ColArgs<double> ca;
+    ColArgs<double> ca{};
     ca.spec = spec; ca.n0 = n[0]; ca.S = S; ca.tx = sig;
     ca.sa = prm->alpha + prm->lambda; ca.sb = prm->theta * prm->k * chat; ca.sscale = 1.0 / (double)N; ca.sinv = 1;
 

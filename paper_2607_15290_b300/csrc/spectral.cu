@@ -277,9 +277,10 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
 
     const double livec = (double)(n0 + n0 / 2 + 1);
     auto run_slot = [&](int slot, double flops) -> cudaError_t {
-        ColArgs<T> ca;
+        ColArgs<T> ca{};
         int batches = 1, mode = 7;
         slot_args<T>(c, slot, sym, ca, batches, mode);
+        ca.skip = io.skip;
         prof_begin(c, K_AXIS, 2 * live * CB, flops);
         cudaError_t err = launch_col_cfg<T>(c, mode, ca, batches, slot_cfg<T>(c, slot, ca.nl));
         prof_end(c);
@@ -307,7 +308,7 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
 
 llg_status plain_axis_pass64(llg_ctx *c, int axis, bool forward) {
     if (axis != 1 || c->geo.dim != 3) return set_error(c, LLG_ERR_INVALID_ARG, "plain axis pass: 3D y axis only");
-    ColArgs<double> ca;
+    ColArgs<double> ca{};
     int batches = 1, mode = 1;
     Symbol sym{1.0, 0.0, 1.0, 0, 0};
     slot_args<double>(c, forward ? SLOT_Y_FWD : SLOT_Y_INV, sym, ca, batches, mode);
@@ -383,7 +384,7 @@ static llg_status tune_prec(llg_ctx *c, std::string *report) {
     static const char *slot_names[] = {"y(2D)", "y-forward", "z", "y-inverse"};
     llg_status st = LLG_OK;
     for (int slot : slots) {
-        ColArgs<T> ca;
+        ColArgs<T> ca{};
         int batches = 1, mode = 7;
         Symbol sym{1.0, 1e-3, 1.0, 1, 0};
         slot_args<T>(c, slot, sym, ca, batches, mode);
