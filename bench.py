@@ -480,9 +480,11 @@ def extras_leg(L, I, ctx, prm, w, m0, args):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1)
     ex["e2e"] = {"value": applies / (t / 1e3), "unit": UNIT, "h2d_bytes_per_step": mh.numel() * 8,
-                 "d2h_bytes_per_step": outh.numel() * 8, "steps": steps,
-                 "note": "each step copies m^n host->device, runs the midpoint step cold (no warm start) "
-                         "and copies m^{n+1} back"}
+                 "d2h_bytes_per_step": outh.numel() * 8, "steps": steps, "ms_per_step": t / steps,
+                 "applies_per_step": applies / steps,
+                 "note": "each step copies m^n host->device, runs the midpoint step cold (no warm start, so "
+                         "more applications per step than the timed warm-started trajectory) and copies "
+                         "m^{n+1} back"}
     return ex
 
 
