@@ -211,7 +211,7 @@ llg_status llg_lower_order_field(llg_ctx *ctx, const llg_params *prm, const doub
 /* ---------------------------------------------------------------- ensembles
    Many independent 2D problems advanced together by projected-Euler steps (Sec. 2.4, 3.2)
    in ONE persistent cooperative kernel launch, captured in a CUDA graph when the stream
-   allows capture (spec batching; the paper solves one problem at a time).  Every
+   allows capture (a batched mode of this library; the paper solves one problem at a time).  Every
    problem has its own grid, damping, time step and field; all advance through the same
    phases in lockstep (right-hand side; flexible GMRES(restart) with the FP32 FFT--HSS
    application and inner matvec, FP64 Arnoldi and least squares; FP64 true residual; the
