@@ -10,6 +10,7 @@
 #include "llg_internal.h"
 #include "krylov.h"
 #include "reduce.cuh"
+#include "convert.cuh"
 
 using namespace llg;
 
@@ -101,7 +102,7 @@ __global__ void k_sum_partials_n(const double *__restrict__ partials, int nb, in
 
 __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, long long n) {
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        b[e] = (float)a[e];
+        b[e] = d2f_rn(a[e]);
 }
 
 // y = s a (s = *scale, or 1 when scale is NULL): the identity "preconditioner"

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include "spectral_kernels.cuh"
 #include "reduce.cuh"
+#include "convert.cuh"
 
 using namespace llg;
 
@@ -387,7 +388,7 @@ __device__ __forceinline__ void ens_xupdate(const EnsProb &P, long long lo, long
     for (long long e = lo + threadIdx.x; e < hi; e += ENS_THREADS) {
         double v = P.x[e];
 #pragma unroll
-        for (int i = 0; i < NV; ++i) v += ys[i] * (double)P.Z[(long long)i * P.n4 + e];
+        for (int i = 0; i < NV; ++i) v += ys[i] * f2d_exact(P.Z[(long long)i * P.n4 + e]);
         P.x[e] = v;
     }
 }
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) ens_kernel(EnsArgs A) {
                 P.x[e] = 0.0;
                 P.V[e] = bv;
                 acc[0] += bv * bv;
-                if (e < 3 * P.N) P.m32[e] = (float)P.m[e];
+                if (e < 3 * P.N) P.m32[e] = d2f_rn(P.m[e]);
             }
             store_partials(A, P, ch, acc, 1);
             __syncthreads();

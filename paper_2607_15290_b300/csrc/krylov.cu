@@ -16,6 +16,7 @@
 #include "llg_internal.h"
 #include "krylov.h"
 #include "reduce.cuh"
+#include "convert.cuh"
 
 namespace llg {
 
@@ -224,7 +225,9 @@ __global__ void __launch_bounds__(RB_THREADS) cycle_update(double *x, const TB *
     __syncthreads();
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         double s = x[e];
-        for (int i = 0; i < jd; ++i) s += cf[i] * (double)B[i * ldb + e];
+        // FP32 basis: widened on the integer pipes (the hardware conversion would take an
+        // FP64 issue slot per element, as many as the multiply-adds)
+        for (int i = 0; i < jd; ++i) s += cf[i] * to_f64(B[i * ldb + e]);
         x[e] = s;
     }
 }

@@ -5,6 +5,7 @@
 #pragma once
 #include "llg_internal.h"
 #include "fft_line.cuh"
+#include "convert.cuh"
 
 namespace llg {
 
@@ -84,25 +85,25 @@ __device__ __forceinline__ void row_fwd_body(const RowArgs<T, TIn, TOut> &a, lon
             const long long j = (2 * (pair0 + gp) + rr) * n0 + xx;
             T u1, u2, u3;
             if constexpr (IN == IN_V) {
-                u1 = s * (T)xv[k][0];
-                u2 = s * (T)xv[k][1];
-                u3 = s * (T)xv[k][2];
+                u1 = s * cvt<T>(xv[k][0]);
+                u2 = s * cvt<T>(xv[k][1]);
+                u3 = s * cvt<T>(xv[k][2]);
             } else if constexpr (IN == IN_M) {
-                u1 = (T)xv[k][0];
-                u2 = (T)xv[k][1];
-                u3 = (T)xv[k][2];
+                u1 = cvt<T>(xv[k][0]);
+                u2 = cvt<T>(xv[k][1]);
+                u3 = cvt<T>(xv[k][2]);
             } else if constexpr (IN == IN_FUSED) {
                 const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];
-                const T v1 = s * (T)xv[k][0], v2 = s * (T)xv[k][1], v3 = s * (T)xv[k][2];
-                const T r = s * (T)xv[k][3];
+                const T v1 = s * cvt<T>(xv[k][0]), v2 = s * cvt<T>(xv[k][1]), v3 = s * cvt<T>(xv[k][2]);
+                const T r = s * cvt<T>(xv[k][3]);
                 u1 = m2 * v3 - m3 * v2 + m1 * r - io.lam * v1;
                 u2 = m3 * v1 - m1 * v3 + m2 * r - io.lam * v2;
                 u3 = m1 * v2 - m2 * v1 + m3 * r - io.lam * v3;
             } else {  // IN_NODAL_T
                 T z4;
-                nodal_inverse<T, true>(mv[k][0], mv[k][1], mv[k][2], io.lam, s * (T)xv[k][0], s * (T)xv[k][1],
-                                       s * (T)xv[k][2], s * (T)xv[k][3], u1, u2, u3, z4);
-                io.y[3 * N + j] = (TOut)(z4 / io.lam);
+                nodal_inverse<T, true>(mv[k][0], mv[k][1], mv[k][2], io.lam, s * cvt<T>(xv[k][0]), s * cvt<T>(xv[k][1]),
+                                       s * cvt<T>(xv[k][2]), s * cvt<T>(xv[k][3]), u1, u2, u3, z4);
+                io.y[3 * N + j] = cvt<TOut>(z4 / io.lam);
             }
             sm[(3 * gp + rr) * LS + RowLayout::idx(xx, 1)] = cmk<C>(u1, u2);
             reinterpret_cast<T *>(&sm[(3 * gp + 2) * LS + RowLayout::idx(xx, 1)])[rr] = u3;
@@ -356,25 +357,25 @@ __device__ __forceinline__ void row_inv_body(const RowArgs<T, TIn, TOut> &a, lon
             const T w3 = reinterpret_cast<const T *>(&sm[(3 * gq + 2) * LS + RowLayout::idx(xx, 1)])[rr];
             TOut *y = io.y;
             if constexpr (OUT == OUT_APPLY) {
-                T z1 = w1, z2 = w2, z3 = w3, z4 = s * (T)xv[k][3] / io.lam;
+                T z1 = w1, z2 = w2, z3 = w3, z4 = s * cvt<T>(xv[k][3]) / io.lam;
                 if (!io.plain_nodal)
                     nodal_inverse<T, false>(mv[k][0], mv[k][1], mv[k][2], io.lam, w1, w2, w3, z4, z1, z2, z3, z4);
-                y[j] = (TOut)z1; y[N + j] = (TOut)z2; y[2 * N + j] = (TOut)z3; y[3 * N + j] = (TOut)z4;
+                y[j] = cvt<TOut>(z1); y[N + j] = cvt<TOut>(z2); y[2 * N + j] = cvt<TOut>(z3); y[3 * N + j] = cvt<TOut>(z4);
             } else if constexpr (OUT == OUT_FUSED) {
                 const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];
-                const T v1 = s * (T)xv[k][0], v2 = s * (T)xv[k][1], v3 = s * (T)xv[k][2];
+                const T v1 = s * cvt<T>(xv[k][0]), v2 = s * cvt<T>(xv[k][1]), v3 = s * cvt<T>(xv[k][2]);
                 T z1 = v1 + w1, z2 = v2 + w2, z3 = v3 + w3, z4 = -(m1 * v1 + m2 * v2 + m3 * v3) / io.lam;
                 if (!io.plain_nodal) nodal_inverse<T, false>(m1, m2, m3, io.lam, z1, z2, z3, z4, z1, z2, z3, z4);
-                y[j] = (TOut)z1; y[N + j] = (TOut)z2; y[2 * N + j] = (TOut)z3; y[3 * N + j] = (TOut)z4;
+                y[j] = cvt<TOut>(z1); y[N + j] = cvt<TOut>(z2); y[2 * N + j] = cvt<TOut>(z3); y[3 * N + j] = cvt<TOut>(z4);
             } else if constexpr (OUT == OUT_MATVEC) {
                 const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];
-                const T v1 = s * (T)xv[k][0], v2 = s * (T)xv[k][1], v3 = s * (T)xv[k][2];
-                const T r = s * (T)xv[k][3];
+                const T v1 = s * cvt<T>(xv[k][0]), v2 = s * cvt<T>(xv[k][1]), v3 = s * cvt<T>(xv[k][2]);
+                const T r = s * cvt<T>(xv[k][3]);
                 const T sg = io.transpose ? (T)-1 : (T)1;
-                y[j] = (TOut)(w1 + sg * (m2 * v3 - m3 * v2 + m1 * r));
-                y[N + j] = (TOut)(w2 + sg * (m3 * v1 - m1 * v3 + m2 * r));
-                y[2 * N + j] = (TOut)(w3 + sg * (m1 * v2 - m2 * v1 + m3 * r));
-                y[3 * N + j] = (TOut)(-sg * (m1 * v1 + m2 * v2 + m3 * v3));
+                y[j] = cvt<TOut>(w1 + sg * (m2 * v3 - m3 * v2 + m1 * r));
+                y[N + j] = cvt<TOut>(w2 + sg * (m3 * v1 - m1 * v3 + m2 * r));
+                y[2 * N + j] = cvt<TOut>(w3 + sg * (m1 * v2 - m2 * v1 + m3 * r));
+                y[3 * N + j] = cvt<TOut>(-sg * (m1 * v1 + m2 * v2 + m3 * v3));
             } else if constexpr (OUT == OUT_FIELD) {
                 T f1 = w1 + io.fld[0], f2 = w2 + io.fld[1], f3 = w3 + io.fld[2];
                 if (io.hf) {
@@ -382,24 +383,24 @@ __device__ __forceinline__ void row_inv_body(const RowArgs<T, TIn, TOut> &a, lon
                     f2 += (T)(io.hs * io.hf[N + j]);
                     f3 += (T)(io.hs * io.hf[2 * N + j]);
                 }
-                y[j] = (TOut)f1;
-                y[N + j] = (TOut)f2;
-                y[2 * N + j] = (TOut)f3;
-                y[3 * N + j] = (TOut)0;
+                y[j] = cvt<TOut>(f1);
+                y[N + j] = cvt<TOut>(f2);
+                y[2 * N + j] = cvt<TOut>(f3);
+                y[3 * N + j] = cvt<TOut>(0);
             } else if constexpr (OUT == OUT_PLAIN) {
-                y[j] = (TOut)w1; y[N + j] = (TOut)w2; y[2 * N + j] = (TOut)w3;
+                y[j] = cvt<TOut>(w1); y[N + j] = cvt<TOut>(w2); y[2 * N + j] = cvt<TOut>(w3);
             } else {  // OUT_JT: (J^T y)_v = w - m^n x y_v + (k/2) r y_v - m^{n+1} y_r ; (J^T y)_r = mhat . y_v
-                const T a1 = s * (T)xv[k][0], a2 = s * (T)xv[k][1], a3 = s * (T)xv[k][2];
-                const T ar = s * (T)xv[k][3];
+                const T a1 = s * cvt<T>(xv[k][0]), a2 = s * cvt<T>(xv[k][1]), a3 = s * cvt<T>(xv[k][2]);
+                const T ar = s * cvt<T>(xv[k][3]);
                 const T n1 = mv[k][0], n2 = mv[k][1], n3 = mv[k][2];
                 const T f1 = fv[k][0], f2 = fv[k][1], f3 = fv[k][2], fr = fv[k][3];
                 const T hk = io.half_k;
                 const T p1 = n1 + 2 * hk * f1, p2 = n2 + 2 * hk * f2, p3 = n3 + 2 * hk * f3;  // m^{n+1}
                 const T h1 = n1 + hk * f1, h2 = n2 + hk * f2, h3 = n3 + hk * f3;              // mhat
-                y[j] = (TOut)(w1 - (n2 * a3 - n3 * a2) + hk * fr * a1 - p1 * ar);
-                y[N + j] = (TOut)(w2 - (n3 * a1 - n1 * a3) + hk * fr * a2 - p2 * ar);
-                y[2 * N + j] = (TOut)(w3 - (n1 * a2 - n2 * a1) + hk * fr * a3 - p3 * ar);
-                y[3 * N + j] = (TOut)(h1 * a1 + h2 * a2 + h3 * a3);
+                y[j] = cvt<TOut>(w1 - (n2 * a3 - n3 * a2) + hk * fr * a1 - p1 * ar);
+                y[N + j] = cvt<TOut>(w2 - (n3 * a1 - n1 * a3) + hk * fr * a2 - p2 * ar);
+                y[2 * N + j] = cvt<TOut>(w3 - (n1 * a2 - n2 * a1) + hk * fr * a3 - p3 * ar);
+                y[3 * N + j] = cvt<TOut>(h1 * a1 + h2 * a2 + h3 * a3);
             }
         }
     }
