@@ -398,8 +398,16 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
     double *dsc = c->dsc, *hsc = c->hsc;
     GmresDev *gh = static_cast<GmresDev *>(c->ghost);
 
+    // ||b||^2 -> dsc[0]; with a caller's initial residual r0 (copied into V_0 or T), ||r0||^2
+    // -> dsc[2] in the same round trip
     if ((st = dot_async(c, b, b, n, dsc)) != LLG_OK) return st;
-    if ((st = sync_read(c, hsc, dsc, sizeof(double))) != LLG_OK) return st;
+    if (r0) {
+        double *dst = flexible ? w.V : w.T;
+        cudaError_t ce = cudaMemcpyAsync(dst, r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+        if ((st = cuda_check(c, ce, "initial residual")) != LLG_OK) return st;
+        if ((st = dot_async(c, dst, dst, n, dsc + 2)) != LLG_OK) return st;
+    }
+    if ((st = sync_read(c, hsc, dsc, (r0 ? 3 : 1) * sizeof(double))) != LLG_OK) return st;
     const double nb = std::sqrt(hsc[0]);
     llg_info inf = llg_info();
     if (nb == 0.0) {
@@ -408,26 +416,23 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
         if (info) *info = inf;
         return LLG_OK;
     }
-    auto true_residual = [&](double *rel) -> llg_status {
+    // the true residual r = b - A x: into T (left) or V_0 (flexible: v_0 = r / ||r||), ||r||^2
+    // into dsc[0]; the caller reads it
+    auto issue_true_residual = [&]() -> llg_status {
         llg_status s2 = ops.matvec(x, w.T);
         if (s2 != LLG_OK) return s2;
-        // the residual overwrites T (left) or lands in V_0 (flexible: v_0 = r / ||r||)
-        if ((s2 = residual_async(c, b, w.T, flexible ? w.V : w.T, n, dsc)) != LLG_OK) return s2;
-        if ((s2 = sync_read(c, hsc, dsc, sizeof(double))) != LLG_OK) return s2;
-        *rel = std::sqrt(hsc[0]) / nb;
-        return LLG_OK;
+        return residual_async(c, b, w.T, flexible ? w.V : w.T, n, dsc);
     };
     double rel;
+    // device location of ||V_0||^2 for the flexible cycle start (V_0 holds the residual itself)
+    const double *v0sq = dsc;
     if (r0) {
-        // the caller's exact initial residual replaces the first matvec
-        double *dst = flexible ? w.V : w.T;
-        cudaError_t ce = cudaMemcpyAsync(dst, r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
-        if ((st = cuda_check(c, ce, "initial residual")) != LLG_OK) return st;
-        if ((st = dot_async(c, dst, dst, n, dsc)) != LLG_OK) return st;
+        rel = std::sqrt(hsc[2]) / nb;
+        v0sq = dsc + 2;
+    } else {
+        if ((st = issue_true_residual()) != LLG_OK) return st;
         if ((st = sync_read(c, hsc, dsc, sizeof(double))) != LLG_OK) return st;
         rel = std::sqrt(hsc[0]) / nb;
-    } else if ((st = true_residual(&rel)) != LLG_OK) {
-        return st;
     }
     w.last_res = flexible ? w.V : w.T;
     const double eta = flexible ? 1e-5 : 0.0;
@@ -442,9 +447,9 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
             if ((st = ops.prec(w.T, nullptr, w.V)) != LLG_OK) return st;
             inf.applies++;
         }
-        if ((st = dot_async(c, w.V, w.V, n, dsc + 1)) != LLG_OK) return st;
+        if (!flexible && (st = dot_async(c, w.V, w.V, n, dsc + 1)) != LLG_OK) return st;
         const double rel_factor = std::max(0.5 * o->rtol / rel, eta);
-        cycle_init<<<1, 32, 0, c->stream>>>(c->gdev, dsc + 1, std::min(rel_factor, 1.0), m);
+        cycle_init<<<1, 32, 0, c->stream>>>(c->gdev, flexible ? v0sq : dsc + 1, std::min(rel_factor, 1.0), m);
         c->launches++;
         const int jmax = std::min(m, o->max_iters - inf.iters);
         const size_t prof_first = c->prof_used;
@@ -473,13 +478,19 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
             cycle_update<double><<<ub, RB_THREADS, 0, c->stream>>>(x, w.V, n, c->gdev, n);
         c->launches += 2;
         if ((st = cuda_check(c, cudaGetLastError(), "cycle update")) != LLG_OK) return st;
-        if ((st = sync_read(c, gh, c->gdev, GMRES_HEADER_BYTES)) != LLG_OK) return st;
+        // the true residual is queued behind the update before the cycle's header is read,
+        // so one host round trip serves both
+        if ((st = issue_true_residual()) != LLG_OK) return st;
+        cudaError_t ce = cudaMemcpyAsync(gh, c->gdev, GMRES_HEADER_BYTES, cudaMemcpyDeviceToHost, c->stream);
+        if ((st = cuda_check(c, ce, "cycle header")) != LLG_OK) return st;
+        if ((st = sync_read(c, hsc, dsc, sizeof(double))) != LLG_OK) return st;
         prof_discard(c, prof_first, gh->jd);
         inf.iters += gh->jd;
         inf.applies += gh->jd;
         inf.restarts++;
         if (gh->breakdown) { result = LLG_ERR_BREAKDOWN; break; }
-        if ((st = true_residual(&rel)) != LLG_OK) return st;
+        rel = std::sqrt(hsc[0]) / nb;
+        v0sq = dsc;
         if (gh->jd == 0) { inf.rel_res_true = rel; result = rel <= o->rtol ? LLG_OK : LLG_ERR_NOT_CONVERGED; break; }
     }
     inf.status = result;
