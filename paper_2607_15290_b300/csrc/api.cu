@@ -585,6 +585,23 @@ llg_status llg_create(const llg_grid *grid, void *cuda_stream, llg_ctx **out) {
     if ((e = cudaMalloc(&c->gdev, sizeof(GmresDev))) != cudaSuccess) return fail(e, "GMRES state");
     if ((e = cudaMemset(c->gdev, 0, sizeof(GmresDev))) != cudaSuccess) return fail(e, "GMRES state");
     if ((e = cudaMallocHost(&c->ghost, sizeof(GmresDev))) != cudaSuccess) return fail(e, "pinned GMRES state");
+    {
+        // progress words the Arnoldi kernels write straight into host memory, so the host can
+        // follow a cycle without synchronising the stream; without mapped memory it polls
+        void *hp = nullptr;
+        int *dp = nullptr;
+        if (cudaHostAlloc(&hp, 64, cudaHostAllocMapped) == cudaSuccess &&
+            cudaHostGetDevicePointer((void **)&dp, hp, 0) == cudaSuccess) {
+            memset(hp, 0, 64);
+            c->hprog = static_cast<volatile int *>(hp);
+            volatile int *dpv = dp;
+            if ((e = cudaMemcpy(&c->gdev->prog, &dpv, sizeof(dpv), cudaMemcpyHostToDevice)) != cudaSuccess)
+                return fail(e, "GMRES progress words");
+        } else {
+            if (hp) cudaFreeHost(hp);
+            cudaGetLastError();
+        }
+    }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "create");
     *out = c;
     return LLG_OK;
@@ -604,6 +621,7 @@ llg_status llg_destroy(llg_ctx *c) {
     for (auto &e : c->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->ghost) cudaFreeHost(c->ghost);
+    if (c->hprog) cudaFreeHost((void *)c->hprog);
     Workspace &w = c->ws;
     cudaFree(w.V); cudaFree(w.Z); cudaFree(w.W); cudaFree(w.T); cudaFree(w.R);
     cudaGetLastError();

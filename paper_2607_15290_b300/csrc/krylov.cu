@@ -79,6 +79,11 @@ __device__ __noinline__ void arnoldi_finish(const double *partials, int nb, int 
         } else if (est <= gd->target || hn == 0.0) {
             gd->done = 1;
         }
+        if (gd->prog) {
+            gd->prog[1] = j + 1;
+            gd->prog[2] = gd->done;
+            __threadfence_system();
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) gd->H[i + GmresDev::LD * j] = col[i];
@@ -186,8 +191,8 @@ __global__ void __launch_bounds__(RB_THREADS, MAXV <= 8 ? 2 : 1) arnoldi_pass_pi
     if (last_block_arrived(&gd->arrived)) arnoldi_finish(partials, gridDim.x, nv, gd, MODE, nv - 1);
 }
 
-// start a cycle: beta = sqrt(red), g = beta e1, scale[0] = 1/beta, target = rel_factor * beta
-__global__ void cycle_init(GmresDev *gd, const double *red_dev, double rel_factor, int m) {
+// start cycle `epoch`: beta = sqrt(red), g = beta e1, scale[0] = 1/beta, target = rel_factor * beta
+__global__ void cycle_init(GmresDev *gd, const double *red_dev, double rel_factor, int m, int epoch) {
     if (threadIdx.x != 0) return;
     const double beta = sqrt(*red_dev);
     gd->m = m;
@@ -201,6 +206,15 @@ __global__ void cycle_init(GmresDev *gd, const double *red_dev, double rel_facto
     if (!(beta > 0.0) || !isfinite(beta)) {
         gd->done = 1;
         gd->breakdown = !isfinite(beta);
+    }
+    gd->epoch = epoch;
+    if (gd->prog) {
+        // the counters first, then the epoch that makes them current
+        gd->prog[1] = 0;
+        gd->prog[2] = gd->done;
+        __threadfence_system();
+        gd->prog[0] = epoch;
+        __threadfence_system();
     }
 }
 
@@ -387,6 +401,35 @@ static llg_status sync_read(llg_ctx *c, void *dst_host, const void *src_dev, siz
     return cuda_check(c, e, "device->host read");
 }
 
+// Wait until the running cycle (number `epoch`) has completed `need` Arnoldi steps or set
+// its stopping flag (*done = 1), reading the progress words the kernels write into host
+// memory; the stream is not synchronised.  Should the stream drain without the words
+// showing either (they are written before each step's last kernel ends), the device
+// header decides.
+static llg_status wait_progress(llg_ctx *c, int epoch, int need, int *done) {
+    volatile int *pw = c->hprog;
+    *done = 0;
+    for (;;) {
+        if (pw[0] == epoch) {
+            const int jd = pw[1], dn = pw[2];
+            if (dn) { *done = 1; return LLG_OK; }
+            if (jd >= need) return LLG_OK;
+        } else if (need <= 0) {
+            return LLG_OK;
+        }
+        const cudaError_t q = cudaStreamQuery(c->stream);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return cuda_check(c, q, "GMRES cycle");
+        // idle stream: every issued step has finished and written its words
+        if (pw[0] == epoch && (pw[2] || pw[1] >= need)) continue;
+        GmresDev *gh = static_cast<GmresDev *>(c->ghost);
+        const llg_status st = sync_read(c, gh, c->gdev, GMRES_HEADER_BYTES);
+        if (st != LLG_OK) return st;
+        *done = gh->done;
+        return LLG_OK;
+    }
+}
+
 llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_opts *o, const double *b, double *x,
                      llg_info *info, const double *r0) {
     llg_status st = ensure_workspace(c, o->restart, flexible);
@@ -449,7 +492,8 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
         }
         if (!flexible && (st = dot_async(c, w.V, w.V, n, dsc + 1)) != LLG_OK) return st;
         const double rel_factor = std::max(0.5 * o->rtol / rel, eta);
-        cycle_init<<<1, 32, 0, c->stream>>>(c->gdev, flexible ? v0sq : dsc + 1, std::min(rel_factor, 1.0), m);
+        const int epoch = ++c->cycle_epoch;
+        cycle_init<<<1, 32, 0, c->stream>>>(c->gdev, flexible ? v0sq : dsc + 1, std::min(rel_factor, 1.0), m, epoch);
         c->launches++;
         const int jmax = std::min(m, o->max_iters - inf.iters);
         const size_t prof_first = c->prof_used;
@@ -465,7 +509,15 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
             }
             if (st != LLG_OK) return st;
             if ((st = arnoldi_step(c, j)) != LLG_OK) return st;
-            if ((j + 1) % c->sync_every == 0 && j + 1 < jmax) {
+            if (j + 1 == jmax) break;
+            if (c->hprog) {
+                // keep one step queued behind the running one: wait for steps 0..j-1, stop once
+                // the cycle's flag is up (at most step j+1 is then issued in vain, and returns
+                // at once)
+                int done = 0;
+                if ((st = wait_progress(c, epoch, j, &done)) != LLG_OK) return st;
+                if (done) break;
+            } else if ((j + 1) % c->sync_every == 0) {
                 if ((st = sync_read(c, gh, c->gdev, GMRES_HEADER_BYTES)) != LLG_OK) return st;
                 if (gh->done) break;
             }

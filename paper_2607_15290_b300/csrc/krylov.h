@@ -23,7 +23,11 @@ struct GmresDev {
     double scale[LD];      // 1 / ||V_i|| of the stored (unnormalised) basis vectors
     double h1[MAXM], h2[MAXM];
     unsigned int arrived;  // blocks of the running Arnoldi pass that have stored their partial sums
-    int pad2;
+    int epoch;             // number of the running cycle (set by cycle_init)
+    // progress words in host-mapped memory, written as the cycle advances:
+    // [0] epoch of the cycle they describe, [1] Arnoldi steps completed, [2] stopping flag.
+    // NULL when mapped memory is unavailable (the host then polls the header).
+    volatile int *prog;
 };
 static constexpr size_t GMRES_HEADER_BYTES = 32;
 

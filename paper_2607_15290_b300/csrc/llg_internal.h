@@ -113,11 +113,13 @@ struct llg_ctx {
     double *hsc = nullptr;       // pinned host mirror of dsc
     llg::GmresDev *gdev = nullptr;
     void *ghost = nullptr;       // pinned host mirror of gdev
+    volatile int *hprog = nullptr;   // host-mapped progress words of the running GMRES cycle
+    int cycle_epoch = 0;         // cycles started through this context
     llg::Workspace ws;
     float *m32 = nullptr;        // FP32 copy of the nodal field (mixed precision)
     double *aux = nullptr;       // 12 N doubles of stepper scratch
     int sm_count = 148;
-    int sync_every = 4;
+    int sync_every = 4;          // blocking-poll interval when hprog is unavailable
     long long launches = 0;      // kernels launched through this context
     llg::ColCfg colcfg[2][llg::NSLOT];   // [FP32, FP64][slot] axis-pass shapes
     bool tuned[2] = {false, false};      // set by llg_autotune
