@@ -395,7 +395,11 @@ __device__ __forceinline__ void ens_xupdate(const EnsProb &P, long long lo, long
 
 // ---------------------------------------------------------------- the persistent kernel
 
-__global__ void __launch_bounds__(ENS_THREADS, 2) ens_kernel(EnsArgs A) {
+// Four blocks per SM (64 registers a thread).  The FP64 loops over large bases spill at that
+// size, but those passes stay bound by FP64 multiply-adds, while the Fourier phases, bound
+// by memory latency, gain from twice the resident warps: the 96-problem run measured
+// 2.24 s at two blocks per SM, 1.99 s at three, 1.90 s at four and 2.06 s at five.
+__global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double s_red[ENS_THREADS / 32][ENS_MAXM];   // block sums of the Gram-Schmidt passes
     EnsState *S = A.st;
