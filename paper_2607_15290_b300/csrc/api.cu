@@ -412,7 +412,7 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
     ops.matvec = [=](const double *xx, double *yy) { return op_matvec64(c, p, theta, m, xx, nullptr, yy, 0); };
     const int pc = o->preconditioner;
     // operators issued inside a GMRES cycle return at once once the cycle's stopping flag
-    // is set (the host polls it only every few iterations); v_0 and the true residual,
+    // is set (the host may have queued one more step); v_0 and the true residual,
     // issued outside cycles, always run
     const int *cyc = &c->gdev->done;
     if (!flex) {

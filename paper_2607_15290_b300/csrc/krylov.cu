@@ -8,9 +8,11 @@
 // normalisation pass is needed.  Dot products reduce per block; the block that
 // finishes a pass last sums the partials in a fixed order (deterministic) and
 // updates the Arnoldi state, so a step is three launches.  The Hessenberg column, Givens
-// rotations, residual estimate and stopping flag live on the device; kernels of
-// later iterations return immediately once the flag is set, so the host only
-// synchronises every few iterations and once per cycle.
+// rotations, residual estimate and stopping flag live on the device, which also writes
+// the completed step count and the flag into host-mapped memory; the host follows them
+// without synchronising the stream, keeps one step queued behind the running one, and
+// synchronises once per cycle.  Kernels of a step issued after the flag was set return
+// immediately.
 #include <cmath>
 #include <algorithm>
 #include "llg_internal.h"
