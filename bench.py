@@ -51,8 +51,8 @@ def peaks():
 # DRAM traffic per launch of the dominant class (dram__bytes_read.sum + dram__bytes_write.sum),
 # from one ncu capture of 90 arnoldi_pass launches of this workload at 128^3 (launches that
 # returned at once left out); to be re-taken whenever the Arnoldi kernels change.
-ARNOLDI_TRAFFIC_BYTES = 385.9e6
-ARNOLDI_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 63 non-empty "
+ARNOLDI_TRAFFIC_BYTES = 371.3e6
+ARNOLDI_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 90 non-empty "
                         "arnoldi_pass launches of this workload (exact-count kernels, fused reduction)")
 
 
