@@ -111,7 +111,11 @@ typedef struct {
 } llg_info;
 
 /* Create a context for one grid; cuda_stream is a cudaStream_t (NULL = legacy default stream).
-   Allocates twiddle/symbol tables and spectral scratch on the current device.
+   Allocates twiddle/symbol tables and spectral scratch on the current device, and 64 bytes
+   of host-mapped memory in which the Arnoldi kernels publish a GMRES cycle's progress, so
+   that the host can follow the cycle without synchronising the stream.  Where mapped memory
+   cannot be had, or when the environment variable LLG_HOST_POLL is "1" at creation, the
+   host instead synchronises every fourth Arnoldi step; results are identical either way.
    Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA. */
 llg_status llg_create(const llg_grid *grid, void *cuda_stream, llg_ctx **out);
 /* Free every device and host resource of the context (synchronises its stream). */

@@ -4,6 +4,7 @@
 // method runs in the kernels of spectral.cu, krylov.cu and below.
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <new>
 #include <vector>
 #include <algorithm>
@@ -590,7 +591,9 @@ llg_status llg_create(const llg_grid *grid, void *cuda_stream, llg_ctx **out) {
         // follow a cycle without synchronising the stream; without mapped memory it polls
         void *hp = nullptr;
         int *dp = nullptr;
-        if (cudaHostAlloc(&hp, 64, cudaHostAllocMapped) == cudaSuccess &&
+        const char *poll = getenv("LLG_HOST_POLL");
+        const bool want = !(poll && strcmp(poll, "1") == 0);
+        if (want && cudaHostAlloc(&hp, 64, cudaHostAllocMapped) == cudaSuccess &&
             cudaHostGetDevicePointer((void **)&dp, hp, 0) == cudaSuccess) {
             memset(hp, 0, 64);
             c->hprog = static_cast<volatile int *>(hp);
