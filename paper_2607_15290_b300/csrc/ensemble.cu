@@ -21,7 +21,7 @@
 #include <vector>
 #include <map>
 #include <algorithm>
-#include "spectral_kernels.cuh"
+#include "spectral_ct.cuh"
 #include "reduce.cuh"
 #include "convert.cuh"
 
@@ -239,6 +239,30 @@ __device__ __forceinline__ void col_dispatch(const ColArgs<T> &c, int TW, int ti
     if (TW == 4) col_body<T, 8, 4, 7>(c, tile, 0, sm);
     else if (TW == 8) col_body<T, 8, 8, 7>(c, tile, 0, sm);
     else col_body<T, 8, 16, 7>(c, tile, 0, sm);
+}
+
+// FP32 phases on the compile-time-length bodies (lines of 128, 256, 512 points, 8 points a
+// thread).  Every class fills the block exactly: a row item is G = 5, 2, 1 row pairs (with
+// one, two, one spare lines of the 256 threads), a column tile is 16, 8, 4 columns wide;
+// two exchange buffers of either shape take the 36 KB of dynamic shared memory.
+template <typename TIn, typename TOut, int IN>
+__device__ __forceinline__ void row_fwd32(const RowArgs<float, TIn, TOut> &a, int ln0, long long grp, unsigned char *sm) {
+    if (ln0 == 7) ct::row_fwd_ct_body<float, TIn, TOut, 7, IN>(a, grp, sm);
+    else if (ln0 == 8) ct::row_fwd_ct_body<float, TIn, TOut, 8, IN>(a, grp, sm);
+    else ct::row_fwd_ct_body<float, TIn, TOut, 9, IN>(a, grp, sm);
+}
+
+template <typename TIn, typename TOut, int OUT>
+__device__ __forceinline__ void row_inv32(const RowArgs<float, TIn, TOut> &a, int ln0, long long grp, unsigned char *sm) {
+    if (ln0 == 7) ct::row_inv_ct_body<float, TIn, TOut, 7, OUT>(a, grp, sm);
+    else if (ln0 == 8) ct::row_inv_ct_body<float, TIn, TOut, 8, OUT>(a, grp, sm);
+    else ct::row_inv_ct_body<float, TIn, TOut, 9, OUT>(a, grp, sm);
+}
+
+__device__ __forceinline__ void col32(const ColArgs<float> &c, int ln1, int tile, unsigned char *sm) {
+    if (ln1 == 7) ct::col_ct_body<float, 7, 8, 16, 7, true>(c, tile, 0, sm);
+    else if (ln1 == 8) ct::col_ct_body<float, 8, 8, 8, 7, true>(c, tile, 0, sm);
+    else ct::col_ct_body<float, 9, 8, 4, 7, true>(c, tile, 0, sm);
 }
 
 // ---------------------------------------------------------------- Arnoldi chunks
@@ -494,7 +518,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     if (S[p].cyc_done) return;
                     auto a = row_args<float, double, float>(P, C, P.V + (long long)j * P.n4, P.Z + (long long)j * P.n4,
                                                            P.m32, &S[p].scale[j]);
-                    row_fwd_body<float, double, float, 8, IN_V>(a, grp, C.nthr_row, smraw);
+                    row_fwd32<double, float, IN_V>(a, C.ln0, grp, smraw);
                     __syncthreads();
                 });
                 if (!bar_sync(A.bar, __LINE__)) return;
@@ -503,7 +527,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     const EnsProb &P = A.prob[p];
                     const EnsClass &C = A.cls[P.cls];
                     if (S[p].cyc_done) return;
-                    col_dispatch<float>(col_args<float>(P, C, P.alpha + P.lam, P.k * P.chat, 1), C.TW, tile, smraw);
+                    col32(col_args<float>(P, C, P.alpha + P.lam, P.k * P.chat, 1), C.ln1, tile, smraw);
                     __syncthreads();
                 });
                 if (!bar_sync(A.bar, __LINE__)) return;
@@ -513,7 +537,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     if (S[p].cyc_done) return;
                     auto a = row_args<float, double, float>(P, C, P.V + (long long)j * P.n4, P.Z + (long long)j * P.n4,
                                                            P.m32, &S[p].scale[j]);
-                    row_inv_body<float, double, float, 8, OUT_APPLY>(a, grp, C.nthr_row, smraw);
+                    row_inv32<double, float, OUT_APPLY>(a, C.ln0, grp, smraw);
                     __syncthreads();
                 });
                 if (!bar_sync(A.bar, __LINE__)) return;
@@ -523,7 +547,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     const EnsClass &C = A.cls[P.cls];
                     if (S[p].cyc_done) return;
                     auto a = row_args<float, float, double>(P, C, P.Z + (long long)j * P.n4, P.W, P.m32, nullptr);
-                    row_fwd_body<float, float, double, 8, IN_V>(a, grp, C.nthr_row, smraw);
+                    row_fwd32<float, double, IN_V>(a, C.ln0, grp, smraw);
                     __syncthreads();
                 });
                 if (!bar_sync(A.bar, __LINE__)) return;
@@ -531,7 +555,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     const EnsProb &P = A.prob[p];
                     const EnsClass &C = A.cls[P.cls];
                     if (S[p].cyc_done) return;
-                    col_dispatch<float>(col_args<float>(P, C, P.alpha, P.k * P.chat, 0), C.TW, tile, smraw);
+                    col32(col_args<float>(P, C, P.alpha, P.k * P.chat, 0), C.ln1, tile, smraw);
                     __syncthreads();
                 });
                 if (!bar_sync(A.bar, __LINE__)) return;
@@ -540,7 +564,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     const EnsClass &C = A.cls[P.cls];
                     if (S[p].cyc_done) return;
                     auto a = row_args<float, float, double>(P, C, P.Z + (long long)j * P.n4, P.W, P.m32, nullptr);
-                    row_inv_body<float, float, double, 8, OUT_MATVEC>(a, grp, C.nthr_row, smraw);
+                    row_inv32<float, double, OUT_MATVEC>(a, C.ln0, grp, smraw);
                     __syncthreads();
                 });
                 if (!bar_sync(A.bar, __LINE__)) return;

@@ -31,8 +31,10 @@ __device__ __forceinline__ void row_fwd_ct_body(const RowArgs<T, TIn, TOut> &a, 
     constexpr int N = 1 << LOGN, E = LineE<T, LOGN>::value, P = N / E, LS = L::size;
     constexpr int LOGP = LOGN - (E == 16 ? 4 : 3);
     const int G = a.G;
+    // one line of LS per P threads: 3 G lines carry data; a block larger than 3 G P (the
+    // ensemble's) transforms its spare lines without storing them
     C *buf0 = reinterpret_cast<C *>(smraw);
-    C *buf1 = buf0 + 3 * G * LS;
+    C *buf1 = buf0 + (blockDim.x / P) * LS;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long Nn = a.N, npairs = a.rows / 2, pair0 = bidx * G;
     const NodalIO<TIn, TOut, T> &io = a.io;
@@ -153,8 +155,9 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
     constexpr int N = 1 << LOGN, E = LineE<T, LOGN>::value, P = N / E, LS = L::size, HN = N / 2;
     constexpr int LOGP = LOGN - (E == 16 ? 4 : 3);
     const int G = a.G;
+    // as in the forward body: spare lines of a block larger than 3 G P carry no data
     C *buf0 = reinterpret_cast<C *>(smraw);
-    C *buf1 = buf0 + 3 * G * LS;
+    C *buf1 = buf0 + (blockDim.x / P) * LS;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long Nn = a.N, npairs = a.rows / 2, pair0 = bidx * G;
     const int line = tid >> LOGP, t = tid & (P - 1);
