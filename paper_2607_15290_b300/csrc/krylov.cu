@@ -95,6 +95,8 @@ template <int MAXV, int MODE>
 __global__ void __launch_bounds__(RB_THREADS) arnoldi_pass(const double *__restrict__ V, long long ldv, int nv,
                                                                 GmresDev *gd, const double *win, double *wout, long long n,
                                                                 double *__restrict__ partials) {
+    pdl_wait();
+    pdl_trigger();
     if (gd->done) return;
     __shared__ double coef[MAXV];
     if (threadIdx.x < nv) {
@@ -148,6 +150,8 @@ template <int MAXV, int MODE>
 __global__ void __launch_bounds__(RB_THREADS, MAXV <= 8 ? 2 : 1) arnoldi_pass_pipe(const double *__restrict__ V, long long ldv, int nv,
                                                                                      GmresDev *gd, const double *win, double *wout,
                                                                                      long long n, double *__restrict__ partials) {
+    pdl_wait();
+    pdl_trigger();
     static_assert(MODE == PASS_DOT || MODE == PASS_UPD_NRM, "pipelined form covers passes A and C");
     if (gd->done) return;
     __shared__ double coef[MAXV];
@@ -195,6 +199,8 @@ __global__ void __launch_bounds__(RB_THREADS, MAXV <= 8 ? 2 : 1) arnoldi_pass_pi
 
 // start cycle `epoch`: beta = sqrt(red), g = beta e1, scale[0] = 1/beta, target = rel_factor * beta
 __global__ void cycle_init(GmresDev *gd, const double *red_dev, double rel_factor, int m, int epoch) {
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x != 0) return;
     const double beta = sqrt(*red_dev);
     gd->m = m;
@@ -222,6 +228,8 @@ __global__ void cycle_init(GmresDev *gd, const double *red_dev, double rel_facto
 
 // y = H^{-1} g (upper triangular, jd x jd); coef_i = y_i * (flexible ? 1 : scale_i)
 __global__ void cycle_backsolve(GmresDev *gd, int flexible) {
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x != 0) return;
     const int jd = gd->jd, ld = GmresDev::LD;
     for (int i = jd - 1; i >= 0; --i) {
@@ -235,6 +243,8 @@ __global__ void cycle_backsolve(GmresDev *gd, int flexible) {
 template <typename TB>
 __global__ void __launch_bounds__(RB_THREADS) cycle_update(double *x, const TB *__restrict__ B, long long ldb,
                                                            const GmresDev *__restrict__ gd, long long n) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double cf[64];
     const int jd = gd->jd;
     if (threadIdx.x < jd) cf[threadIdx.x] = gd->coef[threadIdx.x];
@@ -251,6 +261,8 @@ __global__ void __launch_bounds__(RB_THREADS) cycle_update(double *x, const TB *
 // out = b - t, partial sums of out^2
 __global__ void __launch_bounds__(RB_THREADS) residual_partials(const double *__restrict__ b, const double *t,
                                                                 double *out, long long n, double *partials) {
+    pdl_wait();
+    pdl_trigger();
     double acc[1] = {0.0};
     long long lo, hi;
     block_chunk(n, lo, hi);
@@ -264,6 +276,8 @@ __global__ void __launch_bounds__(RB_THREADS) residual_partials(const double *__
 
 __global__ void __launch_bounds__(RB_THREADS) dot_partials(const double *__restrict__ a, const double *__restrict__ b,
                                                            long long n, double *partials) {
+    pdl_wait();
+    pdl_trigger();
     double acc[1] = {0.0};
     long long lo, hi;
     block_chunk(n, lo, hi);
@@ -272,6 +286,8 @@ __global__ void __launch_bounds__(RB_THREADS) dot_partials(const double *__restr
 }
 
 __global__ void sum_partials(const double *__restrict__ partials, int nb, double *dst) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double tot[1];
     block_sum_partials(partials, nb, 1, tot);
     __syncthreads();
@@ -282,16 +298,16 @@ __global__ void sum_partials(const double *__restrict__ partials, int nb, double
 
 llg_status dot_async(llg_ctx *c, const double *a, const double *b, long long n, double *dst_dev) {
     const int nb = reduction_blocks(c);
-    dot_partials<<<nb, RB_THREADS, 0, c->stream>>>(a, b, n, c->red);
-    sum_partials<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, dst_dev);
+    launch_pdl(dot_partials, dim3(nb), dim3(RB_THREADS), 0, c->stream, a, b, n, c->red);
+    launch_pdl(sum_partials, dim3(1), dim3(RB_THREADS), 0, c->stream, c->red, nb, dst_dev);
     c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "dot");
 }
 
 static llg_status residual_async(llg_ctx *c, const double *b, const double *t, double *out, long long n, double *dst_dev) {
     const int nb = reduction_blocks(c);
-    residual_partials<<<nb, RB_THREADS, 0, c->stream>>>(b, t, out, n, c->red);
-    sum_partials<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, dst_dev);
+    launch_pdl(residual_partials, dim3(nb), dim3(RB_THREADS), 0, c->stream, b, t, out, n, c->red);
+    launch_pdl(sum_partials, dim3(1), dim3(RB_THREADS), 0, c->stream, c->red, nb, dst_dev);
     c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "residual");
 }
@@ -322,7 +338,7 @@ static void launch_pass(llg_ctx *c, int mode, const double *V, long long ldv, in
     {                                                                                     \
         auto k = KERN;                                                                    \
         const int nb = arnoldi_grid(c, k);                                                \
-        k<<<nb, RB_THREADS, 0, c->stream>>>(V, ldv, nv, gd, win, wout, n, c->red);        \
+        launch_pdl(k, dim3(nb), dim3(RB_THREADS), 0, c->stream, V, ldv, nv, gd, win, wout, n, c->red);        \
         return;                                                                           \
     }
     if constexpr (MAXV <= 16) {
@@ -495,7 +511,7 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
         if (!flexible && (st = dot_async(c, w.V, w.V, n, dsc + 1)) != LLG_OK) return st;
         const double rel_factor = std::max(0.5 * o->rtol / rel, eta);
         const int epoch = ++c->cycle_epoch;
-        cycle_init<<<1, 32, 0, c->stream>>>(c->gdev, flexible ? v0sq : dsc + 1, std::min(rel_factor, 1.0), m, epoch);
+        launch_pdl(cycle_init, dim3(1), dim3(32), 0, c->stream, c->gdev, flexible ? v0sq : dsc + 1, std::min(rel_factor, 1.0), m, epoch);
         c->launches++;
         const int jmax = std::min(m, o->max_iters - inf.iters);
         const size_t prof_first = c->prof_used;
@@ -524,12 +540,12 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
                 if (gh->done) break;
             }
         }
-        cycle_backsolve<<<1, 32, 0, c->stream>>>(c->gdev, flexible ? 1 : 0);
+        launch_pdl(cycle_backsolve, dim3(1), dim3(32), 0, c->stream, c->gdev, flexible ? 1 : 0);
         const int ub = reduction_blocks(c) * 2;
         if (flexible)
-            cycle_update<float><<<ub, RB_THREADS, 0, c->stream>>>(x, w.Z, n, c->gdev, n);
+            launch_pdl(cycle_update<float>, dim3(ub), dim3(RB_THREADS), 0, c->stream, x, w.Z, n, c->gdev, n);
         else
-            cycle_update<double><<<ub, RB_THREADS, 0, c->stream>>>(x, w.V, n, c->gdev, n);
+            launch_pdl(cycle_update<double>, dim3(ub), dim3(RB_THREADS), 0, c->stream, x, w.V, n, c->gdev, n);
         c->launches += 2;
         if ((st = cuda_check(c, cudaGetLastError(), "cycle update")) != LLG_OK) return st;
         // the true residual is queued behind the update before the cycle's header is read,

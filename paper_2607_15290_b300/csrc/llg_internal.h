@@ -10,6 +10,30 @@
 
 namespace llg {
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may start while the
+// kernel before it in the stream is still finishing, which hides the launch latency
+// between the many short dependent passes of a GMRES step.  Such a kernel must call
+// pdl_wait() before it touches any memory: it returns once the preceding kernel has
+// completed and its writes are visible.  pdl_trigger() then lets the next kernel begin
+// launching once every block of this one has started.  In a plain launch both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KP, typename... A>
+inline cudaError_t launch_pdl(void (*k)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Spectral buffer layout.  For every grid row (fixed y, z) the x-axis transform
 // stores S complex slots: [0, n0) the full spectrum of the packed pair
 // (c1 + i c2), [n0, n0 + n0/2] the half spectrum of the real component c3,

@@ -43,8 +43,7 @@ static cudaError_t launch_row_fwd_E(llg_ctx *c, int in_mode, RowArgs<T, TIn, TOu
         auto k = row_fwd_kernel<T, TIn, TOut, E, MODE>;                                       \
         cudaError_t e = set_smem(k, sm);                                                      \
         if (e != cudaSuccess) return e;                                                       \
-        k<<<blocks, threads, sm, c->stream>>>(a);                                             \
-        return cudaGetLastError();                                                            \
+        return launch_pdl(k, dim3(blocks), dim3(threads), sm, c->stream, a);                  \
     }
     switch (in_mode) {
         LLG_RF(IN_V) LLG_RF(IN_FUSED) LLG_RF(IN_M) LLG_RF(IN_NODAL_T)
@@ -60,8 +59,7 @@ static cudaError_t launch_row_inv_E(llg_ctx *c, int out_mode, RowArgs<T, TIn, TO
         auto k = row_inv_kernel<T, TIn, TOut, E, MODE>;                                       \
         cudaError_t e = set_smem(k, sm);                                                      \
         if (e != cudaSuccess) return e;                                                       \
-        k<<<blocks, threads, sm, c->stream>>>(a);                                             \
-        return cudaGetLastError();                                                            \
+        return launch_pdl(k, dim3(blocks), dim3(threads), sm, c->stream, a);                  \
     }
     switch (out_mode) {
         LLG_RI(OUT_APPLY) LLG_RI(OUT_FUSED) LLG_RI(OUT_MATVEC) LLG_RI(OUT_FIELD) LLG_RI(OUT_PLAIN) LLG_RI(OUT_JT)
@@ -79,8 +77,7 @@ static cudaError_t launch_col_ETW(llg_ctx *c, int mode, const ColArgs<T> &a, dim
         auto k = col_kernel<T, E, TW, MODE>;                                                  \
         cudaError_t e = set_smem(k, sm);                                                      \
         if (e != cudaSuccess) return e;                                                       \
-        k<<<grid, threads, sm, c->stream>>>(a);                                               \
-        return cudaGetLastError();                                                            \
+        return launch_pdl(k, dim3(grid), dim3(threads), sm, c->stream, a);                    \
     }
     switch (mode) {
         LLG_CK(1) LLG_CK(2) LLG_CK(7)
@@ -100,8 +97,7 @@ static cudaError_t launch_staged_TW(llg_ctx *c, int mode, const ColArgs<float> &
         auto k = col_staged_kernel<8, TWL, CB, MODE>;                                         \
         cudaError_t e = set_smem(k, sm);                                                      \
         if (e != cudaSuccess) return e;                                                       \
-        k<<<grid, threads, sm, c->stream>>>(a, live);                                         \
-        return cudaGetLastError();                                                            \
+        return launch_pdl(k, dim3(grid), dim3(threads), sm, c->stream, a, live);              \
     }
     switch (mode) {
         LLG_CS(1) LLG_CS(2) LLG_CS(7)

@@ -30,8 +30,7 @@ cudaError_t row_fwd_launch(llg_ctx *c, int in_mode, const RowArgs<T, TIn, TOut> 
         auto k = row_fwd_ct<T, TIn, TOut, LOGN, MODE>;                 \
         cudaError_t e = prep(k);                                       \
         if (e != cudaSuccess) return e;                                \
-        k<<<blocks, threads, sm, c->stream>>>(a);                      \
-        return cudaGetLastError();                                     \
+        return launch_pdl(k, dim3(blocks), dim3(threads), sm, c->stream, a); \
     }
     switch (in_mode) {
         LLG_RF(IN_V) LLG_RF(IN_FUSED) LLG_RF(IN_M) LLG_RF(IN_NODAL_T)
@@ -47,8 +46,7 @@ cudaError_t row_inv_launch(llg_ctx *c, int out_mode, const RowArgs<T, TIn, TOut>
         auto k = row_inv_ct<T, TIn, TOut, LOGN, MODE>;                 \
         cudaError_t e = prep(k);                                       \
         if (e != cudaSuccess) return e;                                \
-        k<<<blocks, threads, sm, c->stream>>>(a);                      \
-        return cudaGetLastError();                                     \
+        return launch_pdl(k, dim3(blocks), dim3(threads), sm, c->stream, a); \
     }
     switch (out_mode) {
         LLG_RI(OUT_APPLY) LLG_RI(OUT_FUSED) LLG_RI(OUT_MATVEC) LLG_RI(OUT_FIELD) LLG_RI(OUT_PLAIN) LLG_RI(OUT_JT)
@@ -73,8 +71,7 @@ static cudaError_t col_launch_tw(llg_ctx *c, int mode, const ColArgs<T> &a, dim3
         auto k = col_ct<T, LOGN, E, TW, MODE, DB>;                     \
         cudaError_t e = prep(k);                                       \
         if (e != cudaSuccess) return e;                                \
-        k<<<grid, threads, sm, c->stream>>>(a);                        \
-        return cudaGetLastError();                                     \
+        return launch_pdl(k, dim3(grid), dim3(threads), sm, c->stream, a); \
     }
             switch (mode) {
                 LLG_CK(1) LLG_CK(2) LLG_CK(7)
@@ -110,8 +107,7 @@ static cudaError_t col_v2_launch_tw(llg_ctx *c, int mode, const ColArgs<float> &
         auto k = col_ct_v2<LOGN, TW, MODE, DB>;                        \
         cudaError_t e = prep(k);                                       \
         if (e != cudaSuccess) return e;                                \
-        k<<<grid, threads, sm, c->stream>>>(a);                        \
-        return cudaGetLastError();                                     \
+        return launch_pdl(k, dim3(grid), dim3(threads), sm, c->stream, a); \
     }
         switch (mode) {
             LLG_C2(1) LLG_C2(2) LLG_C2(7)
@@ -142,8 +138,7 @@ static cudaError_t staged_launch_tw(llg_ctx *c, int mode, const ColArgs<float> &
         auto k = col_staged_ct<LOGN, TWL, CB, MODE>;                   \
         cudaError_t e = prep(k);                                       \
         if (e != cudaSuccess) return e;                                \
-        k<<<grid, threads, sm, c->stream>>>(a, live);                  \
-        return cudaGetLastError();                                     \
+        return launch_pdl(k, dim3(grid), dim3(threads), sm, c->stream, a, live); \
     }
         switch (mode) {
             LLG_CS(1) LLG_CS(2) LLG_CS(7)
