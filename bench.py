@@ -127,6 +127,20 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_cpu():
+    """Model name and logical core count of the host, for the CPU-baseline lines."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "host_cores": os.cpu_count()}
+
+
 def oracle_baseline(seconds=12.0):
     """The oracle as it stands, timed on the host cores on a bounded sample: repeated FP64
     FFT--HSS applications of the 128^3 field in the oracle's radix-2 FFT mode."""
@@ -150,7 +164,7 @@ def oracle_baseline(seconds=12.0):
     O.set_transform(O.DFT)
     return {"value": count / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{count} oracle FP64 FFT-HSS applications of the 128^3 field (radix-2 FFT mode, "
-                      f"single thread) in {dt:.1f} s"}
+                      f"single thread) in {dt:.1f} s", **host_cpu()}
 
 
 def run_reference(args):
@@ -179,7 +193,7 @@ def run_reference(args):
            "data": "synthetic", "config": {"workload": WORKLOAD, "reference_step": "one oracle FFT-HSS apply"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{args.steps} oracle FP64 FFT-HSS applications of the 128^3 field "
-                                      "(radix-2 FFT mode, single thread)"},
+                                      "(radix-2 FFT mode, single thread)", **host_cpu()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
