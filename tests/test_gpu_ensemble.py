@@ -21,15 +21,20 @@ def k_explicit(alpha, n):
     return 2 * alpha / ((1 + alpha ** 2) * 2 * (np.pi * n) ** 2)
 
 
-SPECS = [  # (n, alpha, dt / explicit limit, field)
+SPECS = [  # (n, alpha, dt / explicit limit, field); rows and columns of different lengths too
     (128, 0.05, 2.0, "smooth"), (128, 0.3, 16.0, "broadband"),
     (256, 0.1, 4.0, "broadband"), (256, 0.4, 8.0, "smooth"),
     (512, 0.02, 3.0, "smooth"), (512, 0.2, 12.0, "broadband"),
+    ((512, 128), 0.15, 6.0, "broadband"), ((128, 256), 0.08, 5.0, "smooth"),
 ]
 
 
+def shape(n):
+    return n if isinstance(n, tuple) else (n, n)
+
+
 def field(n, kind, seed):
-    return I.smooth2d((n, n), seed=seed) if kind == "smooth" else I.broadband((n, n), seed=seed)
+    return I.smooth2d(shape(n), seed=seed) if kind == "smooth" else I.broadband(shape(n), seed=seed)
 
 
 def test_ensemble_matches_single_problem_path_and_oracle():
@@ -38,9 +43,10 @@ def test_ensemble_matches_single_problem_path_and_oracle():
     probs, refs, m0s = [], [], []
     for i, (n, alpha, c, kind) in enumerate(SPECS):
         m0 = field(n, kind, 300 + i)
-        prm = L.Params(alpha=alpha, k=c * k_explicit(alpha, n), lam=0.5, h_ext=(0.0, 0.0, 0.5))
-        probs.append({"n": (n, n), "params": prm, "m": torch.tensor(m0, device="cuda"),
-                      "x": torch.zeros((4, n, n), dtype=torch.float64, device="cuda")})
+        nn = shape(n)
+        prm = L.Params(alpha=alpha, k=c * k_explicit(alpha, max(nn)), lam=0.5, h_ext=(0.0, 0.0, 0.5))
+        probs.append({"n": nn, "params": prm, "m": torch.tensor(m0, device="cuda"),
+                      "x": torch.zeros((4, nn[1], nn[0]), dtype=torch.float64, device="cuda")})
         m0s.append(m0)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
@@ -49,7 +55,7 @@ def test_ensemble_matches_single_problem_path_and_oracle():
     stream.synchronize()
     for i, ((n, alpha, c, kind), p, info) in enumerate(zip(SPECS, probs, infos)):
         assert info["status"] == 0 and info["rel_res_true"] <= 1e-10, (i, info)
-        ctx = L.Context((n, n))
+        ctx = L.Context(shape(n))
         m = torch.tensor(m0s[i], device="cuda")
         for _ in range(2):
             m, x, _ = L.llg_step_euler(ctx, p["params"], opts, m)
