@@ -96,7 +96,6 @@ __global__ void __launch_bounds__(RB_THREADS) arnoldi_pass(const double *__restr
                                                                 GmresDev *gd, const double *win, double *wout, long long n,
                                                                 double *__restrict__ partials) {
     pdl_wait();
-    pdl_trigger();
     if (gd->done) return;
     __shared__ double coef[MAXV];
     if (threadIdx.x < nv) {
@@ -151,7 +150,6 @@ __global__ void __launch_bounds__(RB_THREADS, MAXV <= 8 ? 2 : 1) arnoldi_pass_pi
                                                                                      GmresDev *gd, const double *win, double *wout,
                                                                                      long long n, double *__restrict__ partials) {
     pdl_wait();
-    pdl_trigger();
     static_assert(MODE == PASS_DOT || MODE == PASS_UPD_NRM, "pipelined form covers passes A and C");
     if (gd->done) return;
     __shared__ double coef[MAXV];
@@ -200,7 +198,6 @@ __global__ void __launch_bounds__(RB_THREADS, MAXV <= 8 ? 2 : 1) arnoldi_pass_pi
 // start cycle `epoch`: beta = sqrt(red), g = beta e1, scale[0] = 1/beta, target = rel_factor * beta
 __global__ void cycle_init(GmresDev *gd, const double *red_dev, double rel_factor, int m, int epoch) {
     pdl_wait();
-    pdl_trigger();
     if (threadIdx.x != 0) return;
     const double beta = sqrt(*red_dev);
     gd->m = m;
@@ -229,7 +226,6 @@ __global__ void cycle_init(GmresDev *gd, const double *red_dev, double rel_facto
 // y = H^{-1} g (upper triangular, jd x jd); coef_i = y_i * (flexible ? 1 : scale_i)
 __global__ void cycle_backsolve(GmresDev *gd, int flexible) {
     pdl_wait();
-    pdl_trigger();
     if (threadIdx.x != 0) return;
     const int jd = gd->jd, ld = GmresDev::LD;
     for (int i = jd - 1; i >= 0; --i) {
@@ -244,7 +240,6 @@ template <typename TB>
 __global__ void __launch_bounds__(RB_THREADS) cycle_update(double *x, const TB *__restrict__ B, long long ldb,
                                                            const GmresDev *__restrict__ gd, long long n) {
     pdl_wait();
-    pdl_trigger();
     __shared__ double cf[64];
     const int jd = gd->jd;
     if (threadIdx.x < jd) cf[threadIdx.x] = gd->coef[threadIdx.x];
@@ -262,7 +257,6 @@ __global__ void __launch_bounds__(RB_THREADS) cycle_update(double *x, const TB *
 __global__ void __launch_bounds__(RB_THREADS) residual_partials(const double *__restrict__ b, const double *t,
                                                                 double *out, long long n, double *partials) {
     pdl_wait();
-    pdl_trigger();
     double acc[1] = {0.0};
     long long lo, hi;
     block_chunk(n, lo, hi);
@@ -277,7 +271,6 @@ __global__ void __launch_bounds__(RB_THREADS) residual_partials(const double *__
 __global__ void __launch_bounds__(RB_THREADS) dot_partials(const double *__restrict__ a, const double *__restrict__ b,
                                                            long long n, double *partials) {
     pdl_wait();
-    pdl_trigger();
     double acc[1] = {0.0};
     long long lo, hi;
     block_chunk(n, lo, hi);
@@ -287,7 +280,6 @@ __global__ void __launch_bounds__(RB_THREADS) dot_partials(const double *__restr
 
 __global__ void sum_partials(const double *__restrict__ partials, int nb, double *dst) {
     pdl_wait();
-    pdl_trigger();
     __shared__ double tot[1];
     block_sum_partials(partials, nb, 1, tot);
     __syncthreads();

@@ -10,14 +10,14 @@
 
 namespace llg {
 
-// Programmatic dependent launch.  A kernel launched with launch_pdl may start while the
-// kernel before it in the stream is still finishing, which hides the launch latency
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be launched before
+// the kernel ahead of it in the stream has retired, which hides most of the launch latency
 // between the many short dependent passes of a GMRES step.  Such a kernel must call
 // pdl_wait() before it touches any memory: it returns once the preceding kernel has
-// completed and its writes are visible.  pdl_trigger() then lets the next kernel begin
-// launching once every block of this one has started.  In a plain launch both are no-ops.
+// completed and its writes are visible (in a plain launch it is a no-op).  No kernel
+// signals its dependents early: letting the next grid's blocks onto the SMs while this
+// grid's last wave still runs made the FP64 passes of mid-size grids up to 20% slower.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KP, typename... A>
 inline cudaError_t launch_pdl(void (*k)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {

@@ -142,7 +142,6 @@ __device__ __forceinline__ void row_fwd_ct_body(const RowArgs<T, TIn, TOut> &a, 
 template <typename T, typename TIn, typename TOut, int LOGN, int IN>
 __global__ void __launch_bounds__(512) row_fwd_ct(RowArgs<T, TIn, TOut> a) {
     pdl_wait();
-    pdl_trigger();
     if (a.io.skip && *a.io.skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     row_fwd_ct_body<T, TIn, TOut, LOGN, IN>(a, blockIdx.x, smraw);
@@ -295,7 +294,6 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
 template <typename T, typename TIn, typename TOut, int LOGN, int OUT>
 __global__ void __launch_bounds__(512) row_inv_ct(RowArgs<T, TIn, TOut> a) {
     pdl_wait();
-    pdl_trigger();
     if (a.io.skip && *a.io.skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     row_inv_ct_body<T, TIn, TOut, LOGN, OUT>(a, blockIdx.x, smraw);
@@ -357,7 +355,6 @@ template <typename T, int LOGN, int E, int TW, int MODE, bool DB>
 __global__ void __launch_bounds__(TW *((1 << LOGN) / E), (sizeof(T) == 4 && TW * ((1 << LOGN) / E) <= 512) ? 2 : 1)
     col_ct(ColArgs<T> a) {
     pdl_wait();
-    pdl_trigger();
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     col_ct_body<T, LOGN, E, TW, MODE, DB>(a, blockIdx.x, blockIdx.y, smraw);
@@ -368,7 +365,6 @@ __global__ void __launch_bounds__(TW *((1 << LOGN) / E), (sizeof(T) == 4 && TW *
 template <int LOGN, int TW, int MODE, bool DB>
 __global__ void __launch_bounds__((TW / 2) * ((1 << LOGN) / LineE<float, LOGN>::value), 2) col_ct_v2(ColArgs<float> a) {
     pdl_wait();
-    pdl_trigger();
     if (a.skip && *a.skip) return;
     using C = float2;
     constexpr int N = 1 << LOGN, E = LineE<float, LOGN>::value, P = N / E;
@@ -405,7 +401,6 @@ __global__ void __launch_bounds__((TW / 2) * ((1 << LOGN) / LineE<float, LOGN>::
 template <int LOGN, int TWL, int CB, int MODE>
 __global__ void __launch_bounds__(CB *((1 << LOGN) / 8)) col_staged_ct(ColArgs<float> a, int live) {
     pdl_wait();
-    pdl_trigger();
     if (a.skip && *a.skip) return;
     using C = float2;
     constexpr int N = 1 << LOGN, E = 8, P = N / E;

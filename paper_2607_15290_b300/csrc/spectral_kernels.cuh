@@ -146,7 +146,6 @@ __device__ __forceinline__ void row_fwd_body(const RowArgs<T, TIn, TOut> &a, lon
 template <typename T, typename TIn, typename TOut, int E, int IN>
 __global__ void __launch_bounds__(512) row_fwd_kernel(RowArgs<T, TIn, TOut> a) {
     pdl_wait();
-    pdl_trigger();
     if (a.io.skip && *a.io.skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     row_fwd_body<T, TIn, TOut, E, IN>(a, blockIdx.x, blockDim.x, smraw);
@@ -188,7 +187,6 @@ __device__ __forceinline__ void col_body(const ColArgs<T> &a, int bx, int by, un
 template <typename T, int E, int TW, int MODE>
 __global__ void __launch_bounds__(512, (sizeof(T) == 4 && E <= 8) ? 2 : 1) col_kernel(ColArgs<T> a) {
     pdl_wait();
-    pdl_trigger();
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     col_body<T, E, TW, MODE>(a, blockIdx.x, blockIdx.y, smraw);
@@ -215,7 +213,6 @@ template <int TWL> struct StagedRow { static constexpr int value = TWL + ((8 - (
 template <int E, int TWL, int CB, int MODE>
 __global__ void __launch_bounds__(512) col_staged_kernel(ColArgs<float> a, int live) {
     pdl_wait();
-    pdl_trigger();
     if (a.skip && *a.skip) return;
     using C = float2;
     constexpr int SROW = StagedRow<TWL>::value;
@@ -415,7 +412,6 @@ __device__ __forceinline__ void row_inv_body(const RowArgs<T, TIn, TOut> &a, lon
 template <typename T, typename TIn, typename TOut, int E, int OUT>
 __global__ void __launch_bounds__(512) row_inv_kernel(RowArgs<T, TIn, TOut> a) {
     pdl_wait();
-    pdl_trigger();
     if (a.io.skip && *a.io.skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     row_inv_body<T, TIn, TOut, E, OUT>(a, blockIdx.x, blockDim.x, smraw);
