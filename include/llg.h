@@ -269,7 +269,8 @@ enum {
     LLG_KCLASS_ARNOLDI = 4   /* Gram--Schmidt passes over the Krylov basis */
 };
 /* Start timing every launch of one kernel class on this context: a CUDA event pair is
-   recorded on the context's stream around each launch, together with the launch's
+   recorded on the context's stream around each launch (around the three passes of an
+   Arnoldi step for that class, counted as three launches), together with the launch's
    algorithmic bytes and flops (inputs read + outputs written once; 5 n log2 n flops per
    complex length-n transform; 2 per multiply-add).  Launches of an Arnoldi step that the
    device-side stopping flag turned into no-ops are discarded. */

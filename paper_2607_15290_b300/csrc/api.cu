@@ -29,7 +29,7 @@ llg_status cuda_check(llg_ctx *c, cudaError_t e, const char *what) {
                      std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-void prof_begin(llg_ctx *c, int cls, double bytes, double flops, int tag) {
+void prof_begin(llg_ctx *c, int cls, double bytes, double flops, int tag, int count) {
     c->prof_open = -1;
     if (c->prof_class == 0 || cls != c->prof_class) return;
     if (c->prof_used == c->prof.size()) {
@@ -46,6 +46,7 @@ void prof_begin(llg_ctx *c, int cls, double bytes, double flops, int tag) {
     e.flops = flops;
     e.tag = tag;
     e.valid = 1;
+    e.count = count;
     cudaEventRecord(e.a, c->stream);
     c->prof_open = (int)c->prof_used++;
 }
@@ -672,7 +673,7 @@ llg_status llg_profile_end(llg_ctx *c, double *total_ms, long long *launches, do
         ms += t;
         by += e.bytes;
         fl += e.flops;
-        ++n;
+        n += e.count;
     }
     c->prof_class = 0;
     c->prof_used = 0;

@@ -360,24 +360,19 @@ static void pass_dispatch_raw(llg_ctx *c, int mode, const double *V, long long l
     else launch_pass<64>(c, mode, V, ldv, nv, win, wout, n);
 }
 
-static void pass_dispatch(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const double *win, double *wout,
-                          long long n, int j) {
-    const double nd = (double)n;
-    const double bytes = 8.0 * nd * (mode == PASS_DOT ? nv + 1 : nv + 2);
-    const double flops = nd * (mode == PASS_DOT ? 2.0 * nv : (mode == PASS_UPD_DOT ? 4.0 * nv : 2.0 * nv + 2.0));
-    prof_begin(c, K_ARNOLDI, bytes, flops, j);
-    pass_dispatch_raw(c, mode, V, ldv, nv, win, wout, n);
-    prof_end(c);
-}
-
 // one Arnoldi step j on w = W (CGS2); writes the unnormalised V_{j+1}
 static llg_status arnoldi_step(llg_ctx *c, int j) {
     Workspace &w = c->ws;
     const long long n = w.n;
     const int nv = j + 1;
-    pass_dispatch(c, PASS_DOT, w.V, n, nv, w.W, nullptr, n, j);
-    pass_dispatch(c, PASS_UPD_DOT, w.V, n, nv, w.W, w.W, n, j);
-    pass_dispatch(c, PASS_UPD_NRM, w.V, n, nv, w.W, w.V + (long long)(j + 1) * n, n, j);
+    // algorithmic bytes and flops of the three passes: (nv + 1) + 2 (nv + 2) words and
+    // nv + 2 nv + (nv + 1) multiply-adds per unknown; profiled as one interval of 3 launches
+    const double nd = (double)n;
+    prof_begin(c, K_ARNOLDI, 8.0 * nd * (3.0 * nv + 5.0), nd * (8.0 * nv + 2.0), j, 3);
+    pass_dispatch_raw(c, PASS_DOT, w.V, n, nv, w.W, nullptr, n);
+    pass_dispatch_raw(c, PASS_UPD_DOT, w.V, n, nv, w.W, w.W, n);
+    pass_dispatch_raw(c, PASS_UPD_NRM, w.V, n, nv, w.W, w.V + (long long)(j + 1) * n, n);
+    prof_end(c);
     c->launches += 3;
     return cuda_check(c, cudaGetLastError(), "arnoldi");
 }

@@ -149,7 +149,7 @@ struct llg_ctx {
     bool tuned[2] = {false, false};      // set by llg_autotune
     std::string err;
     // live per-kernel-class timing (llg_profile_begin/end): one event pair per launch
-    struct ProfEntry { cudaEvent_t a, b; double bytes, flops; int tag; int valid; };
+    struct ProfEntry { cudaEvent_t a, b; double bytes, flops; int tag; int valid; int count; };
     int prof_class = 0;
     std::vector<ProfEntry> prof;
     size_t prof_used = 0;
@@ -166,7 +166,9 @@ llg_status cuda_check(llg_ctx *c, cudaError_t e, const char *what);
 // live profiling of one kernel class: call prof_begin right before a launch and
 // prof_end right after it; both are no-ops unless that class is being profiled.
 enum KClass { K_NONE = 0, K_XFWD = 1, K_AXIS = 2, K_XINV = 3, K_ARNOLDI = 4 };
-void prof_begin(llg_ctx *c, int cls, double bytes, double flops, int tag = -1);
+// count: launches the timed interval covers (the Arnoldi passes of a step are timed as one
+// interval, so that no events sit between their launches)
+void prof_begin(llg_ctx *c, int cls, double bytes, double flops, int tag = -1, int count = 1);
 void prof_end(llg_ctx *c);
 void prof_discard(llg_ctx *c, size_t first, int min_tag);
 
