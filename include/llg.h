@@ -280,6 +280,17 @@ llg_status llg_profile_end(llg_ctx *ctx, double *total_ms, long long *launches, 
 /* Measure the device's multiply-add rate with a register-resident FMA loop on the context's
    stream (fp64 != 0: double, else float); *tflops receives 2 * FMAs / s / 1e12 (HOST). */
 llg_status llg_probe_fma_rate(llg_ctx *ctx, int fp64, double *tflops);
+/* Self-check with no counterpart in the paper.  The mixed-precision path converts between
+   float and double with integer operations instead of the hardware conversions (which run
+   at the FP64 multiply-add rate on this part) and relies on both giving the same bits.
+   This compares them on the device: float -> double on all 2^32 float bit patterns, double
+   -> float (round to nearest even) on n_doubles hashed patterns, a quarter each arbitrary,
+   in and around the float exponent range, on or beside a rounding tie, and at ties in the
+   float subnormal range.  The mismatch counts (NaN against NaN matches) go to the HOST
+   pointers.  Runs on the context's stream and synchronises it; allocates 16 bytes.
+   Errors: INVALID_ARG (null pointer, n_doubles < 0), OOM/CUDA. */
+llg_status llg_check_conversions(llg_ctx *ctx, long long n_doubles, long long *f2d_mismatches,
+                                 long long *d2f_mismatches);
 
 #ifdef __cplusplus
 }

@@ -149,6 +149,13 @@ class Context:
         self._check(self.lib.llg_probe_fma_rate(self.h, int(fp64), C.byref(out)))
         return out.value
 
+    def check_conversions(self, n_doubles=1 << 26):
+        """Compare the integer-pipe float<->double conversions with the hardware ones on the
+        device (all 2^32 floats, n_doubles hashed doubles); returns the two mismatch counts."""
+        f, d = C.c_longlong(), C.c_longlong()
+        self._check(self.lib.llg_check_conversions(self.h, int(n_doubles), C.byref(f), C.byref(d)))
+        return f.value, d.value
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.llg_destroy(self.h)

@@ -36,7 +36,7 @@ EXPORTS = [
     "llg_lower_order_field",
     "llg_ensemble_create", "llg_ensemble_run", "llg_ensemble_set_blocks", "llg_ensemble_max_blocks",
     "llg_ensemble_autotune", "llg_ensemble_destroy", "llg_ensemble_last_error",
-    "llg_autotune", "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate",
+    "llg_autotune", "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate", "llg_check_conversions",
 ]
 KCLASS = {"xfwd": 1, "axis": 2, "xinv": 3, "arnoldi": 4}
 
@@ -117,6 +117,7 @@ def lib():
     L.llg_profile_begin.argtypes = [ctx, C.c_int]
     L.llg_profile_end.argtypes = [ctx, d, P(C.c_longlong), d, d]
     L.llg_probe_fma_rate.argtypes = [ctx, C.c_int, d]
+    L.llg_check_conversions.argtypes = [ctx, C.c_longlong, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     for name in EXPORTS:
         if name not in ("llg_last_error", "llg_launch_count", "llg_nodes", "llg_ensemble_last_error"):
             getattr(L, name).restype = C.c_int

@@ -66,6 +66,60 @@ void prof_discard(llg_ctx *c, size_t first, int min_tag) {
 
 // ------------------------------------------------------------------ small kernels
 
+// Self-check of the integer-pipe conversions (convert.cuh) against the hardware ones.
+// Floats: every bit pattern u in [first, first + count).  Doubles: `count` patterns from a
+// counter-based hash, mixed so that a quarter are arbitrary, a quarter have exponents in
+// and around the float range, a quarter sit on or next to a rounding tie, and a quarter are
+// ties in the float subnormal range.  Mismatches (NaN against NaN counts as a match) are
+// added to bad[0] (float -> double) and bad[1] (double -> float).
+__device__ __forceinline__ unsigned long long conv_hash(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__global__ void k_conv_check_f2d(unsigned long long first, unsigned long long count, unsigned long long *bad) {
+    unsigned long long local = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const float f = __uint_as_float((unsigned)(first + i));
+        const double a = (double)f, b = f2d_exact(f);
+        const bool same = __double_as_longlong(a) == __double_as_longlong(b) || (a != a && b != b);
+        local += same ? 0ull : 1ull;
+    }
+    if (local) atomicAdd(&bad[0], local);
+}
+
+__global__ void k_conv_check_d2f(unsigned long long seed, unsigned long long count, unsigned long long *bad) {
+    unsigned long long local = 0;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long u = conv_hash(seed + 2 * i);
+        const unsigned long long r = conv_hash(seed + 2 * i + 1);
+        const unsigned kind = (unsigned)(i & 3);
+        if (kind == 1) {
+            const unsigned long long ex = 856ull + (r >> 33) % 400ull;
+            u = (u & 0x800fffffffffffffull) | (ex << 52);
+        } else if (kind == 2) {
+            const unsigned long long ex = 866ull + (r >> 40) % 300ull, t = (r >> 20) & 3ull;
+            u = (u & 0x800fffffe0000000ull) | (ex << 52) |
+                (t == 0 ? 0x10000000ull : (t == 1 ? 0x0fffffffull : 0x10000001ull));
+        } else if (kind == 3) {
+            const unsigned long long ex = 866ull + (r >> 40) % 31ull;
+            const int sh = 926 - (int)ex;
+            unsigned long long m = u & 0xfffffffffffffull;
+            if (sh >= 1 && sh <= 52) m = (m & ~((1ull << sh) - 1ull)) | (1ull << (sh - 1));
+            u = (u & 0x8000000000000000ull) | (ex << 52) | m;
+        }
+        const double d = __longlong_as_double((long long)u);
+        const float a = (float)d, b = d2f_rn(d);
+        const bool same = __float_as_uint(a) == __float_as_uint(b) || (a != a && b != b);
+        local += same ? 0ull : 1ull;
+    }
+    if (local) atomicAdd(&bad[1], local);
+}
+
 template <typename T>
 __global__ void k_fma_probe(T *out, int iters) {
     T a[8];
@@ -709,6 +763,36 @@ llg_status llg_probe_fma_rate(llg_ctx *c, int fp64, double *tflops) {
     c->launches += 2;
     if (e != cudaSuccess) return cuda_check(c, e, "probe");
     *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
+    return LLG_OK;
+}
+
+llg_status llg_check_conversions(llg_ctx *c, long long n_doubles, long long *f2d_mismatches,
+                                 long long *d2f_mismatches) {
+    LLG_GUARD(c);
+    if (!f2d_mismatches || !d2f_mismatches || n_doubles < 0) return set_error(c, LLG_ERR_INVALID_ARG, "bad argument");
+    unsigned long long *bad = nullptr;
+    cudaError_t e = cudaMalloc(&bad, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_check(c, e, "conversion check buffer");
+    e = cudaMemsetAsync(bad, 0, 2 * sizeof(unsigned long long), c->stream);
+    const int blocks = c->sm_count * 16, threads = 256;
+    const unsigned long long slice = 1ull << 30;   // all 2^32 float patterns in four launches
+    for (unsigned long long first = 0; e == cudaSuccess && first < (1ull << 32); first += slice) {
+        k_conv_check_f2d<<<blocks, threads, 0, c->stream>>>(first, slice, bad);
+        e = cudaGetLastError();
+        c->launches++;
+    }
+    if (e == cudaSuccess && n_doubles > 0) {
+        k_conv_check_d2f<<<blocks, threads, 0, c->stream>>>(0x5EEDull, (unsigned long long)n_doubles, bad);
+        e = cudaGetLastError();
+        c->launches++;
+    }
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, bad, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(bad);
+    if (e != cudaSuccess) return cuda_check(c, e, "conversion check");
+    *f2d_mismatches = (long long)h[0];
+    *d2f_mismatches = (long long)h[1];
     return LLG_OK;
 }
 
