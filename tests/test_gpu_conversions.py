@@ -16,3 +16,10 @@ def test_integer_conversions_match_hardware():
     f2d, d2f = ctx.check_conversions(1 << 26)
     assert (f2d, d2f) == (0, 0)
     ctx.close()
+
+
+def test_check_conversions_rejects_negative_count():
+    ctx = L.Context((8, 8))
+    with pytest.raises(L.LLGError):
+        ctx.check_conversions(-1)
+    ctx.close()
