@@ -596,7 +596,8 @@ int orc_step_midpoint(const orc_grid *g, const orc_params *p, const orc_opts *o,
 
 /*
  * The converged midpoint step solves R(v, r) = 0 with mhat = m^n + (k/2) v:
- *   R_v = alpha v + (k/2) Chat (-Lap) v + Chat (-Lap) m^n + mhat x v + mhat r - (1+alpha^2) h
+ *   R_v = alpha v + (k/2) Chat (-Lap) v + Chat (-Lap) m^n + mhat x v + mhat r - (1+alpha^2) h_j
+ *   (h_j = h + h_field_j, the applied field at node j)
  *   R_r = -mhat . v
  * Its Jacobian in (v, r):
  *   J_vv = alpha I + (k/2) Chat (-Lap) + [m^n]x + (k/2) r I,  J_vr = mhat,  J_rv = -(m^n + k v)^T.
@@ -672,9 +673,11 @@ int orc_adjoint_midpoint(const orc_grid *g, const orc_params *p, const orc_opts 
             /* (dR/dm^n)^T y = Chat(-Lap) y_v + v x y_v + r y_v - v y_r */
             double t = chat * lap_y[c * N + j] + vxy[c] + r[j] * yv[c] - vv[c] * yr;
             mbar_n[c * N + j] = mbar_next[c * N + j] - t;
-            /* dR_v/dalpha = v + alpha k c_ex (-Lap) v + 2 alpha c_ex (-Lap) m^n - 2 alpha h */
+            /* dR_v/dalpha = v + alpha k c_ex (-Lap) v + 2 alpha c_ex (-Lap) m^n - 2 alpha h_j,
+             * h_j = h + h_field_j: the whole applied field enters R_v through (1+alpha^2) h_low */
+            double hj = q.h[c] + (q.h_field ? q.h_field[c * N + j] : 0.0);
             double dra = vv[c] + q.alpha * q.k * q.c_ex * lap_v[c * N + j]
-                       + 2.0 * q.alpha * q.c_ex * lap_m[c * N + j] - 2.0 * q.alpha * q.h[c];
+                       + 2.0 * q.alpha * q.c_ex * lap_m[c * N + j] - 2.0 * q.alpha * hj;
             da -= yv[c] * dra;
             dhx[c] += s * yv[c];
         }

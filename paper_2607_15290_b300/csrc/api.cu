@@ -286,11 +286,12 @@ __global__ void k_adj_prep(const double *__restrict__ m, const double *__restric
 }
 
 // mbar_n = mbar_next - [Chat(-Lap) y_v + v x y_v + r y_v - v y_r];
-// partial sums of -y_v . (v + (-Lap) u - 2 alpha h) and of y_v (per component)
+// partial sums of -y_v . (v + (-Lap) u - 2 alpha h_j) and of y_v (per component), with
+// h_j = h + hf_j the applied field at node j (hf may be NULL: zero)
 __global__ void k_adj_final(const double *__restrict__ mbar_next, const double *__restrict__ y,
                             const double *__restrict__ lapy, const double *__restrict__ xf,
                             const double *__restrict__ lapu, double alpha, double h0, double h1, double h2,
-                            double *mbar_n, long long N, double *partials) {
+                            const double *__restrict__ hf, double *mbar_n, long long N, double *partials) {
     long long lo, hi;
     block_chunk(N, lo, hi);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -303,7 +304,8 @@ __global__ void k_adj_final(const double *__restrict__ mbar_next, const double *
         for (int q = 0; q < 3; ++q) {
             const long long e = q * N + j;
             mbar_n[e] = mbar_next[e] - (lapy[e] + cx[q] + r * yv[q] - vv[q] * yr);
-            acc[0] -= yv[q] * (vv[q] + lapu[e] - 2.0 * alpha * h[q]);
+            const double hq = hf ? h[q] + hf[e] : h[q];
+            acc[0] -= yv[q] * (vv[q] + lapu[e] - 2.0 * alpha * hq);
             acc[1 + q] += yv[q];
         }
     }
@@ -1091,7 +1093,7 @@ llg_status llg_adjoint_step(llg_ctx *c, const llg_params *p, const llg_opts *o, 
         if ((st = spectral_chain<double, double, double>(c, IN_V, OUT_PLAIN, io2, s2)) != LLG_OK) return st;
     }
     k_adj_final<<<nb, RB_THREADS, 0, c->stream>>>(mbar_next, y, lapy, x, lapu, p->alpha, p->h_ext[0], p->h_ext[1],
-                                                  p->h_ext[2], mbar_n, N, c->red);
+                                                  p->h_ext[2], p->h_field, mbar_n, N, c->red);
     k_sum_partials_n<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, 4, c->dsc);
     c->launches += 2;
     if ((st = cuda_check(c, cudaGetLastError(), "adjoint")) != LLG_OK) return st;

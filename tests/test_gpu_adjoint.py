@@ -86,6 +86,40 @@ def _adjoint_vs_oracle(n, k):
     assert np.abs(dm - dm_o).max() <= 1e-8 * np.abs(dm_o).max()
 
 
+@pytest.mark.parametrize("n,k", [((32, 16), 2e-3), ((64, 128), 2e-5)])
+def test_adjoint_step_with_nodal_field_matches_oracle(n, k):
+    """One converged midpoint step with a per-node applied field h_field: the adjoint's
+    mbar_n, d/dalpha (which carries -2 alpha (h + h_field_j) in dR_v/dalpha) and d/dh
+    against the oracle's adjoint of the same step, 1e-8 relative.  Both take the step's
+    (m^n, v, r) from the oracle's forward, so only the adjoints are compared."""
+    if n[0] >= 64:
+        O.set_transform(O.FFT)
+    try:
+        og = O.Grid(n)
+        ctx = L.Context(n)
+        m0 = I.smooth2d(n, seed=51, noise=0.05)
+        mbar = I.smooth2d(n, seed=52, noise=0.3)
+        hf = 2.0 * np.random.default_rng(53).standard_normal((3, n[1], n[0]))
+        alpha, h = 0.3, (0.1, -0.2, 0.5)
+        po = O.Params(alpha=alpha, k=k, theta=0.5, lam=0.5, h=h, h_field=hf)
+        oo = O.Opts(rtol=1e-13, picard_tol=1e-14, picard_max=100)
+        _, x, _ = O.step_midpoint(og, po, oo, m0)
+        mb_o, da_o, dh_o, _ = O.adjoint_midpoint(og, po, oo, m0, x, mbar)
+        _, da_0, _, _ = O.adjoint_midpoint(og, O.Params(alpha=alpha, k=k, theta=0.5, lam=0.5, h=h), oo, m0, x, mbar)
+        # dropping the field term would miss the 1e-8 comparison below by more than 1000x
+        assert abs(da_o - da_0) > 1e3 * 1e-8 * abs(da_o)
+        dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
+        pl = L.Params(alpha=alpha, k=k, theta=0.5, lam=0.5, h_ext=h, h_field=dev(hf))
+        mb, da, dh, info = L.llg_adjoint_step(ctx, pl, L.Opts(rtol=1e-13, restart=30), dev(m0), dev(x), dev(mbar))
+        assert info["rel_res_true"] <= 1e-12
+        assert abs(da - da_o) <= 1e-8 * abs(da_o), (da, da_o)
+        assert np.abs(np.array(dh) - dh_o).max() <= 1e-8 * np.abs(dh_o).max()
+        mbh = mb.cpu().numpy()
+        assert np.abs(mbh - mb_o).max() <= 1e-8 * np.abs(mb_o).max()
+    finally:
+        O.set_transform(O.DFT)
+
+
 def test_adjoint_vs_central_differences_512sq_16_steps():
     """512^2 grid, 16 midpoint steps at dt = 8x the explicit exchange limit, checkpoint every 4
     steps, smooth seeded target: directional derivatives in alpha, h and m0 from the adjoint
@@ -108,12 +142,13 @@ def test_adjoint_vs_central_differences_512sq_16_steps():
     # m - m_target cancels ~700-fold: the step-1e-6 difference is good to ~1e-5 here.  The
     # map is nearly linear in h over T ~ 5e-6, so step 1e-3 has negligible truncation error
     # and gives the 1e-6 comparison.
-    for eps_h, tol in ((1e-6, 1e-4), (1e-3, 1e-6)):
+    # every component of h: z at both steps, x and y at step 1e-3
+    for comp, eps_h, tol in ((2, 1e-6, 1e-4), (2, 1e-3, 1e-6), (0, 1e-3, 1e-6), (1, 1e-3, 1e-6)):
         hp, hm = list(h), list(h)
-        hp[2] += eps_h
-        hm[2] -= eps_h
+        hp[comp] += eps_h
+        hm[comp] -= eps_h
         fd_h = central_difference(f(alpha, hp, m0), f(alpha, hm, m0), tgt, eps_h)
-        assert abs(fd_h - dh[2]) <= tol * abs(dh[2]), (eps_h, fd_h, dh[2])
+        assert abs(fd_h - dh[comp]) <= tol * abs(dh[comp]), (comp, eps_h, fd_h, dh[comp])
     d = torch.tensor(I.smooth2d(n, seed=43, noise=1.0), device="cuda")
     fd_m = central_difference(f(alpha, h, m0 + eps * d), f(alpha, h, m0 - eps * d), tgt, eps)
     ad_m = float((dm0 * d).sum())

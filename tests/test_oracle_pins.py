@@ -523,3 +523,37 @@ def test_adjoint_matches_central_differences():
     d = np.random.default_rng(21).standard_normal(m0.shape)
     fd = (L(prm, m0 + eps * d) - L(prm, m0 - eps * d)) / (2 * eps)
     assert abs(fd - np.sum(dm0 * d)) <= 1e-6 * max(abs(fd), 1e-3)
+
+
+def test_adjoint_alpha_with_nodal_field():
+    """d/dalpha with a per-node applied field: R_v carries -(1+alpha^2)(h + h_field_j), so
+    dR_v/dalpha has -2 alpha (h + h_field_j) (Sec. 3.3 eqs. (C-N), (hatm)).  Central
+    differences of the dense-solve forward pin the adjoint's alpha derivative, and the
+    field term is large enough here that dropping it fails the check."""
+    import dataclasses
+    g = O.Grid((4, 4))
+    m0 = I.smooth2d(g.n, seed=23, noise=0.05)
+    tgt = I.smooth2d(g.n, seed=24, noise=0.3)
+    hf = 2.0 * np.random.default_rng(25).standard_normal((3,) + g.shape)
+    prm = O.Params(alpha=0.3, k=2e-3, h=(0.1, -0.2, 0.5), h_field=hf)
+    opts = O.Opts(use_dense=1, picard_tol=1e-15, picard_max=200)
+    nsteps = 3
+    _, da, dh, _, _ = O.midpoint_loss_grad(g, prm, opts, m0, tgt, nsteps)
+    _, da0, _, _, _ = O.midpoint_loss_grad(g, dataclasses.replace(prm, h_field=np.zeros_like(hf)), opts, m0, tgt,
+                                           nsteps)
+
+    def L(prm_):
+        ms, _, _ = O.run_midpoint(g, prm_, opts, m0, nsteps)
+        return 0.5 * float(np.sum((ms[-1] - tgt) ** 2))
+
+    eps = 1e-6
+    fd_a = (L(dataclasses.replace(prm, alpha=prm.alpha + eps))
+            - L(dataclasses.replace(prm, alpha=prm.alpha - eps))) / (2 * eps)
+    assert abs(fd_a - da) <= 1e-6 * max(abs(da), 1e-3)
+    # the nodal field changes the alpha derivative by far more than the tolerance
+    assert abs(da - da0) > 1e3 * 1e-6 * max(abs(da), 1e-3)
+    for c in range(3):
+        hp = list(prm.h); hm = list(prm.h)
+        hp[c] += eps; hm[c] -= eps
+        fd = (L(dataclasses.replace(prm, h=tuple(hp))) - L(dataclasses.replace(prm, h=tuple(hm)))) / (2 * eps)
+        assert abs(fd - dh[c]) <= 1e-6 * max(abs(dh[c]), 1e-3)
