@@ -141,10 +141,81 @@ def host_cpu():
     return {"cpu_model": model, "host_cores": os.cpu_count()}
 
 
-def oracle_baseline(seconds=12.0):
-    """The oracle as it stands, timed on the host cores on a bounded sample: repeated FP64
-    FFT--HSS applications of the 128^3 field in the oracle's radix-2 FFT mode."""
+def _oracle_inputs_file(n):
+    """The 128^3 workload's field and a saddle vector, written once to a temporary .npz so
+    that worker processes load them instead of regenerating them."""
     import numpy as np
+    from paper_2607_15290_b300 import inputs as I
+    f = tempfile.NamedTemporaryFile(suffix=".npz", delete=False)
+    f.close()
+    np.savez(f.name, m=I.smooth3d(n), p=I.random_saddle_vector(n, seed=5))
+    return f.name
+
+
+def _oracle_apply_worker(path, n, prm_kw, warmup, count):
+    """One single-threaded oracle process: `warmup` untimed then `count` timed FP64 FFT--HSS
+    applications (radix-2 FFT mode).  Returns (wall-clock start, end) of the timed ones."""
+    import numpy as np
+    import oracle as O
+    d = np.load(path)
+    m, p = d["m"], d["p"]
+    g = O.Grid(n)
+    prm = O.Params(**prm_kw)
+    O.set_transform(O.FFT)
+    for _ in range(warmup):
+        O.ffthss_apply(g, prm, m, p)
+    t0 = time.time()
+    for _ in range(count):
+        O.ffthss_apply(g, prm, m, p)
+    return t0, time.time()
+
+
+def _oracle_processes():
+    """Independent oracle processes to run at once: one per logical core, capped by the
+    available host memory (about 0.7 GB per 128^3 process)."""
+    cores = os.cpu_count() or 1
+    try:
+        with open("/proc/meminfo") as f:
+            avail = next(int(l.split()[1]) for l in f if l.startswith("MemAvailable")) / 2 ** 20
+        cores = max(1, min(cores, int(avail / 1.0)))
+    except (OSError, StopIteration, ValueError):
+        pass
+    return cores
+
+
+def oracle_apply_throughput(procs, warmup, count):
+    """Oracle FFT--HSS applications/s with `procs` independent single-threaded processes
+    (spawned), each doing `warmup` + `count` applications of the 128^3 field; the oracle's
+    arithmetic is unchanged, the processes only run side by side.  Rate = procs * count /
+    (last end - first start of the timed applications)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    w = workload_params()
+    prm_kw = dict(alpha=w["alpha"], k=w["k"], theta=0.5, lam=w["lam"], h=w["h"])
+    path = _oracle_inputs_file(w["n"])
+    try:
+        with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as pool:
+            futs = [pool.submit(_oracle_apply_worker, path, w["n"], prm_kw, warmup, count) for _ in range(procs)]
+            spans = [f.result() for f in futs]
+    finally:
+        os.unlink(path)
+    t0 = min(a for a, _ in spans)
+    t1 = max(b for _, b in spans)
+    return procs * count / (t1 - t0), t1 - t0
+
+
+def oracle_baseline(iters_per_solve=None, solves_per_step=None, seconds=10.0):
+    """The oracle as it stands on the host cores, on bounded samples of the 128^3 workload:
+      * single thread: FP64 FFT--HSS applications (radix-2 FFT mode) for ~`seconds`, and one
+        saddle matvec;
+      * all cores: one independent single-threaded oracle process per core (memory allowing),
+        two applications each after one untimed;
+      * one GMRES solve and one midpoint step, extrapolated from the single-thread apply and
+        matvec times with the GPU run's iterations per solve and solves per step (each
+        oracle GMRES iteration is one matvec and one application; the initial and final
+        residuals add two more of each; the Gram--Schmidt work is left out, so these are
+        lower bounds).  A full oracle solve at this size takes about a minute or more,
+        which does not fit a bounded sample."""
     import oracle as O
     from paper_2607_15290_b300 import inputs as I
     w = workload_params()
@@ -153,6 +224,7 @@ def oracle_baseline(seconds=12.0):
     m = I.smooth3d(w["n"])
     p = I.random_saddle_vector(w["n"], seed=5)
     O.set_transform(O.FFT)
+    O.ffthss_apply(g, prm, m, p)
     t0 = time.perf_counter()
     count = 0
     while True:
@@ -161,39 +233,49 @@ def oracle_baseline(seconds=12.0):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    O.saddle_apply(g, prm, m, p)
+    matvec_s = time.perf_counter() - t1
     O.set_transform(O.DFT)
-    return {"value": count / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{count} oracle FP64 FFT-HSS applications of the 128^3 field (radix-2 FFT mode, "
-                      f"single thread) in {dt:.1f} s", **host_cpu()}
+    apply_s = dt / count
+    procs = _oracle_processes()
+    rate_all, span = oracle_apply_throughput(procs, 1, 2)
+    out = {"value": rate_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+           "sample": f"{procs} independent single-threaded oracle processes, 2 FP64 FFT-HSS applications each "
+                     f"of the 128^3 field (radix-2 FFT mode) after 1 untimed, {span:.1f} s",
+           "single_thread": {"value": count / dt, "unit": UNIT, "cores": 1,
+                             "sample": f"{count} applications in {dt:.1f} s",
+                             "apply_s": apply_s, "saddle_matvec_s": matvec_s},
+           **host_cpu()}
+    if iters_per_solve is not None:
+        solve_s = (iters_per_solve + 2) * (apply_s + matvec_s)
+        out["single_thread"]["solve_s_extrapolated"] = solve_s
+        out["single_thread"]["extrapolation"] = (
+            f"(iterations per solve {iters_per_solve:.2f} + 2) x (apply + matvec), Gram-Schmidt left out: lower bound")
+        if solves_per_step is not None:
+            out["single_thread"]["step_s_extrapolated"] = solve_s * solves_per_step
+            out["single_thread"]["solves_per_step"] = solves_per_step
+    return out
 
 
 def run_reference(args):
+    """The oracle on the host cores as the reference arm: each step is one FP64 FFT--HSS
+    application of the 128^3 field in every one of `procs` independent single-threaded
+    oracle processes (one per core, memory allowing); value = applications/s of all of them."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np
-    import oracle as O
-    from paper_2607_15290_b300 import inputs as I
-    w = workload_params()
-    g = O.Grid(w["n"])
-    prm = O.Params(alpha=w["alpha"], k=w["k"], theta=0.5, lam=w["lam"], h=w["h"])
-    m = I.smooth3d(w["n"])
-    p = I.random_saddle_vector(w["n"], seed=5)
-    O.set_transform(O.FFT)
-    for _ in range(args.warmup):
-        O.ffthss_apply(g, prm, m, p)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.ffthss_apply(g, prm, m, p)
-    dt = time.perf_counter() - t0
-    value = args.steps / dt
+    procs = _oracle_processes()
+    value, span = oracle_apply_throughput(procs, args.warmup, args.steps)
+    sample = (f"{procs} independent single-threaded oracle processes, {args.steps} FP64 FFT-HSS applications "
+              f"each of the 128^3 field (radix-2 FFT mode) after {args.warmup} untimed")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": span / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "reference_step": "one oracle FFT-HSS apply"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"{args.steps} oracle FP64 FFT-HSS applications of the 128^3 field "
-                                      "(radix-2 FFT mode, single thread)", **host_cpu()},
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "reference_step": f"one oracle FFT-HSS apply in each of {procs} processes"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample,
+                            **host_cpu()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -206,7 +288,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--roofline-class", default="arnoldi", choices=["xfwd", "axis", "xinv", "arnoldi"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, apply sweep and e2e legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and apply sweep legs")
     ap.add_argument("--apply-sweep", default="", help="only time the isolated FFT-HSS apply on these grids, "
                     "e.g. '256^3,128^3,1024^2' (one JSON line each, with a per-pass breakdown)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --apply-sweep")
@@ -283,6 +365,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # the timed trajectory's starting state, kept in pinned host memory for the end-to-end leg
+    start_m = mA.cpu().pin_memory()
+    start_v = vprev.cpu().pin_memory()
+
     clocks = Clocks(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = ctx.launches()
@@ -312,6 +398,7 @@ def main():
 
     extras = {}
     pk = peaks()
+    e2e = end_to_end(L, ctx, prm, opts, start_m, start_v, args.steps)
     if not args.no_extras and rank == 0:
         extras = extras_leg(L, I, ctx, prm, w, m0, args)
     fp64_peak = ctx.probe_fma_rate(True)
@@ -346,17 +433,51 @@ def main():
                    "parallelism": f"replicas x{world} (independent problems, no collective)"},
         "solves_per_s": totals["solves"] / (ms / 1e3), "steps_per_s": totals["steps"] / (ms / 1e3),
         "gmres_iters_per_solve": iters / max(solves, 1), "max_len_drift": drift,
-        "roofline": roof, "gpu_launches": gpu_launches, "clocks": clk,
+        "roofline": roof, "gpu_launches": gpu_launches, "clocks": clk, "e2e": e2e,
         "fp64_fma_tflops_measured": fp64_peak, "fp32_fma_tflops_measured": fp32_peak,
         "autotune": tuning.strip().splitlines(),
     }
     out.update(extras)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = oracle_baseline()
+        out["cpu_baseline"] = oracle_baseline(iters / max(solves, 1), totals["solves"] / totals["steps"])
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def end_to_end(L, ctx, prm, opts, start_m, start_v, steps):
+    """The timed trajectory again, from the same starting state, through host buffers: every
+    step copies m^n and v^{n-1/2} from pinned host memory to the device, runs the midpoint
+    step through the C ABI and copies m^{n+1} and v^{n+1/2} back to the same host buffers,
+    which feed the next step.  Same steps, same warm start, same work per step as the timed
+    region, so ms_per_step compares directly; the copies are inside the timed region."""
+    import torch
+    mh = start_m.clone().pin_memory()
+    vh = start_v.clone().pin_memory()
+    md, vd, mo, xx = ctx.empty(3), ctx.empty(3), ctx.empty(3), ctx.empty(4)
+    stream = ctx.stream
+    applies = 0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(steps):
+        md.copy_(mh, non_blocking=True)
+        vd.copy_(vh, non_blocking=True)
+        _, _, info = L.llg_step_midpoint(ctx, prm, opts, md, vd, mo, xx)
+        mh.copy_(mo, non_blocking=True)
+        vh.copy_(xx[:3], non_blocking=True)
+        applies += info["applies"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - w0) * 1e3
+    t = e0.elapsed_time(e1)
+    return {"value": applies / (t / 1e3), "unit": UNIT, "h2d_bytes_per_step": (mh.numel() + vh.numel()) * 8,
+            "d2h_bytes_per_step": (mh.numel() + vh.numel()) * 8, "steps": steps, "ms_per_step": t / steps,
+            "wall_ms_per_step": wall / steps, "applies_per_step": applies / steps,
+            "note": "the timed trajectory from its starting state, with m^n and v^{n-1/2} copied in from pinned "
+                    "host memory and m^{n+1}, v^{n+1/2} copied back every step"}
 
 
 def cufft_apply_compare(L, I, ctx, prm, nn, ours_ms):
@@ -407,8 +528,8 @@ def cufft_apply_compare(L, I, ctx, prm, nn, ours_ms):
 
 
 def extras_leg(L, I, ctx, prm, w, m0, args):
-    """FP32-flexible vs all-FP64 solve of one identical system, the isolated apply sweep and
-    the end-to-end (host buffer) figure.  Runs after the timed region."""
+    """FP32-flexible vs all-FP64 solve of one identical system and the isolated apply sweep.
+    Runs after the timed region."""
     import torch
     ex = {}
     n = w["n"]
@@ -475,30 +596,6 @@ def extras_leg(L, I, ctx, prm, w, m0, args):
     c256.close()
     torch.cuda.empty_cache()
 
-    # end to end through host buffers: H2D of m^n from pinned memory, the step, D2H of m^{n+1}
-    opts = L.Opts(restart=30, rtol=1e-10, precision=L.PREC_FP32_FLEX, picard_tol=1e-10)
-    mh = m0.cpu().pin_memory()
-    outh = torch.empty_like(mh).pin_memory()
-    md, mo, xx = ctx.empty(3), ctx.empty(3), ctx.empty(4)
-    steps = max(2, min(args.steps, 5))
-    applies = 0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
-        md.copy_(mh, non_blocking=True)
-        _, _, info = L.llg_step_midpoint(ctx, prm, opts, md, None, mo, xx)
-        outh.copy_(mo, non_blocking=True)
-        applies += info["applies"]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1)
-    ex["e2e"] = {"value": applies / (t / 1e3), "unit": UNIT, "h2d_bytes_per_step": mh.numel() * 8,
-                 "d2h_bytes_per_step": outh.numel() * 8, "steps": steps, "ms_per_step": t / steps,
-                 "applies_per_step": applies / steps,
-                 "note": "each step copies m^n host->device, runs the midpoint step cold (no warm start, so "
-                         "more applications per step than the timed warm-started trajectory) and copies "
-                         "m^{n+1} back"}
     return ex
 
 
@@ -714,19 +811,9 @@ def ensemble_leg(args):
     import torch
     import paper_2607_15290_b300 as L
     from paper_2607_15290_b300 import inputs as I
-    rng = np.random.default_rng(20260725)
     steps = 5
-    specs = []
-    for n in (128, 256, 512):
-        for i in range(32):
-            alpha = float(rng.uniform(0.01, 0.5))
-            c = float(rng.uniform(2.0, 16.0))
-            w = float(rng.uniform(0.0, 1.0))
-            k = c * 2 * alpha / ((1 + alpha ** 2) * 2 * (np.pi * n) ** 2)
-            seed = 1000 * n + i
-            f = w * I.smooth2d((n, n), seed=seed) + (1 - w) * I.broadband((n, n), seed=seed)
-            f = f / np.sqrt((f * f).sum(0, keepdims=True))
-            specs.append((n, alpha, k, f))
+    specs = [(n, alpha, c * 2 * alpha / ((1 + alpha ** 2) * 2 * (np.pi * n) ** 2), f)
+             for n, alpha, c, f in I.ensemble_mix()]
     opts = L.Opts(restart=30, rtol=1e-10, max_iters=900, precision=L.PREC_FP32_FLEX)
     stream = torch.cuda.Stream()
     probs = [{"n": (n, n), "params": L.Params(alpha=a, k=k, lam=0.5, h_ext=(0.0, 0.0, 0.5)),

@@ -197,7 +197,10 @@ llg_status llg_step_midpoint(llg_ctx *ctx, const llg_params *prm, const llg_opts
    (v, r), solves J^T y = (k mbar_next, 0) by GMRES preconditioned with M(mhat)^{-T}, then
    mbar_n = mbar_next - (dR/dm^n)^T y, *dalpha -= y^T dR/dalpha, dh[c] -= y^T dR/dh_c.
    m_n: 3 planes; x: the step's (v | r) (4 planes); mbar_next, mbar_n: 3 planes (device).
-   dalpha, dh: HOST pointers, accumulated (+=).  Uniform applied field only. FP64. */
+   dalpha, dh: HOST pointers, accumulated (+=).  The applied field is h_ext plus the optional
+   per-node prm->h_field (the same field the forward step used): both enter dR_v/dalpha through
+   -2 alpha (h_ext + h_field_j); dh is the gradient with respect to the uniform h_ext.  Demag
+   and anisotropy are refused (INVALID_ARG).  FP64. */
 llg_status llg_adjoint_step(llg_ctx *ctx, const llg_params *prm, const llg_opts *opts,
                             const double *m_n, const double *x, const double *mbar_next,
                             double *mbar_n, double *dalpha, double dh[3], llg_info *info);
@@ -244,6 +247,15 @@ int llg_ensemble_max_blocks(const llg_ensemble *ens);
 /* Pick the persistent block count by timing one step for each multiple of the SM count up to
    the co-resident limit (problems' m restored afterwards); *blocks (HOST) receives the choice. */
 llg_status llg_ensemble_autotune(llg_ensemble *ens, int *blocks);
+/* Diagnostics of the persistent kernel's grid barrier (no counterpart in the paper).  Every
+   barrier wait gives up after budget_cycles SM clock cycles (0: the default, about 2 s), sets an
+   error flag and returns; all blocks then leave the kernel and llg_ensemble_run returns
+   LLG_ERR_TIMEOUT with the barrier's source line in llg_ensemble_last_error.  hold_block >= 0
+   makes that block withhold its arrival at the first barrier and return (-1: none), so the
+   others' waits run out: this exercises the timeout path without any unbounded wait.  The
+   ensemble stays usable after a timeout (restore budget 0, hold -1 and run again).
+   INVALID_ARG for budget_cycles < 0 or hold_block < -1. */
+llg_status llg_ensemble_set_barrier_test(llg_ensemble *ens, long long budget_cycles, int hold_block);
 llg_status llg_ensemble_destroy(llg_ensemble *ens);
 const char *llg_ensemble_last_error(const llg_ensemble *ens);
 

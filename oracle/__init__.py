@@ -391,6 +391,20 @@ def run_midpoint(grid: Grid, prm: Params, opts: Opts, m0, nsteps):
     return ms, xs, infos
 
 
+def run_euler(grid: Grid, prm: Params, opts: Opts, m0, nsteps, transform=None):
+    """Run ``nsteps`` projected Euler steps; returns (m after the last step, infos).  With
+    ``transform`` set (DFT or FFT), that transform mode is selected first: this makes the call
+    self-contained for a worker process, whose module state starts at the default."""
+    if transform is not None:
+        set_transform(transform)
+    m = _f64(m0, (3,) + grid.shape)
+    infos = []
+    for _ in range(nsteps):
+        m, _, info = step_euler(grid, prm, opts, m)
+        infos.append(info)
+    return m, infos
+
+
 def midpoint_loss_grad(grid: Grid, prm: Params, opts: Opts, m0, m_target, nsteps):
     """L = 1/2 sum |m^N - m_target|^2 and its gradient w.r.t. (alpha, h, m0) by the
     step-by-step adjoint of the converged midpoint map."""

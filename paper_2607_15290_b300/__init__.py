@@ -302,6 +302,13 @@ class Ensemble:
             raise LLGError(st, self.lib.llg_ensemble_last_error(self.h).decode())
         return b.value
 
+    def set_barrier_test(self, budget_cycles=0, hold_block=-1):
+        """Diagnostics: shorten the grid barrier's wait limit (0: default) and make one block
+        withhold its first arrival (-1: none); see llg_ensemble_set_barrier_test."""
+        st = self.lib.llg_ensemble_set_barrier_test(self.h, int(budget_cycles), int(hold_block))
+        if st != 0:
+            raise LLGError(st, "llg_ensemble_set_barrier_test failed")
+
     def run(self, steps):
         """Returns (infos in caller order, used_graph)."""
         infos = (_abi.Info * self.count)()

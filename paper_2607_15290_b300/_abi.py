@@ -35,7 +35,7 @@ EXPORTS = [
     "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy",
     "llg_lower_order_field",
     "llg_ensemble_create", "llg_ensemble_run", "llg_ensemble_set_blocks", "llg_ensemble_max_blocks",
-    "llg_ensemble_autotune", "llg_ensemble_destroy", "llg_ensemble_last_error",
+    "llg_ensemble_autotune", "llg_ensemble_set_barrier_test", "llg_ensemble_destroy", "llg_ensemble_last_error",
     "llg_autotune", "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate", "llg_check_conversions",
 ]
 KCLASS = {"xfwd": 1, "axis": 2, "xinv": 3, "arnoldi": 4}
@@ -111,6 +111,7 @@ def lib():
     L.llg_ensemble_set_blocks.argtypes = [vp, C.c_int]
     L.llg_ensemble_max_blocks.argtypes = [vp]
     L.llg_ensemble_autotune.argtypes = [vp, P(C.c_int)]
+    L.llg_ensemble_set_barrier_test.argtypes = [vp, C.c_longlong, C.c_int]
     L.llg_ensemble_destroy.argtypes = [vp]
     L.llg_ensemble_last_error.argtypes = [vp]
     L.llg_ensemble_last_error.restype = C.c_char_p

@@ -81,13 +81,17 @@ constexpr long long BARRIER_BUDGET = 4000000000LL;   // clock64 cycles (about 2 
 
 // Bounded grid-wide barrier.  Thread 0 of each block arrives on the counter; the last
 // arrival resets it and advances the generation; the others wait for the generation to
-// change, giving up after BARRIER_BUDGET cycles.  Returns false (for the whole block)
-// once any block has given up.  Memory written before the barrier is visible after it
-// (fences on both sides of the arrival).
-__device__ __forceinline__ bool bar_sync(EnsBarrier *b, int where) {
+// change, giving up after `budget` cycles.  Returns false (for the whole block) once any
+// block has given up.  Memory written before the barrier is visible after it (fences on
+// both sides of the arrival).  Block `hold` (diagnostics; -1 in normal runs) does not
+// arrive and returns false at once, so the others' waits run out: every block still
+// returns, and the host reads the error flag.
+__device__ __forceinline__ bool bar_wait(EnsBarrier *b, int where, long long budget, int hold) {
     __shared__ int s_ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && (int)blockIdx.x == hold) {
+        s_ok = 0;
+    } else if (threadIdx.x == 0) {
         volatile unsigned *vgen = &b->gen;
         volatile int *verr = &b->err;
         const unsigned g0 = *vgen;
@@ -102,7 +106,7 @@ __device__ __forceinline__ bool bar_sync(EnsBarrier *b, int where) {
             const long long t0 = clock64();
             while (*vgen == g0) {
                 if (*verr) { ok = 0; break; }
-                if (clock64() - t0 > BARRIER_BUDGET) {
+                if (clock64() - t0 > budget) {
                     atomicExch(&b->err, 1);
                     atomicMax(&b->where, where);
                     ok = 0;
@@ -135,7 +139,13 @@ struct EnsArgs {
     long long nchunks;
     long long row_items[3], col_items[3];   // per class item counts
     int cls_of_group_offset;   // unused
+    long long budget;          // barrier wait limit (clock64 cycles)
+    int hold_block;            // diagnostics: block that withholds its arrival (-1: none)
 };
+
+__device__ __forceinline__ bool bar_sync(const EnsArgs &A, int where) {
+    return bar_wait(A.bar, where, A.budget, A.hold_block);
+}
 
 // ---------------------------------------------------------------- item decoding
 
@@ -438,14 +448,14 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
             row_fwd_body<double, double, double, 8, IN_M>(a, grp, C.nthr_row, smraw);
             __syncthreads();
         });
-        if (!bar_sync(A.bar, __LINE__)) return;
+        if (!bar_sync(A, __LINE__)) return;
         for_col_items(A, [&](int p, int tile) {
             const EnsProb &P = A.prob[p];
             const EnsClass &C = A.cls[P.cls];
             col_dispatch<double>(col_args<double>(P, C, 0.0, -P.chat, 0), C.TW, tile, smraw);
             __syncthreads();
         });
-        if (!bar_sync(A.bar, __LINE__)) return;
+        if (!bar_sync(A, __LINE__)) return;
         for_row_items(A, [&](int p, long long grp) {
             const EnsProb &P = A.prob[p];
             const EnsClass &C = A.cls[P.cls];
@@ -455,7 +465,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
             row_inv_body<double, double, double, 8, OUT_FIELD>(a, grp, C.nthr_row, smraw);
             __syncthreads();
         });
-        if (!bar_sync(A.bar, __LINE__)) return;
+        if (!bar_sync(A, __LINE__)) return;
         // ---- x = 0, V_0 = b, ||b||^2, FP32 copy of m
         for_chunk_items(A, [&](int p, int ch) {
             const EnsProb &P = A.prob[p];
@@ -474,7 +484,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
             __syncthreads();
         });
         if (blockIdx.x == 0 && tid == 0) { A.flags[0] = 0; A.flags[1] = 0; A.flags[2] = 0; }
-        if (!bar_sync(A.bar, __LINE__)) return;
+        if (!bar_sync(A, __LINE__)) return;
         for (int p = blockIdx.x; p < A.nprob; p += gridDim.x) {
             const EnsProb &P = A.prob[p];
             __shared__ double tot[ENS_MAXM];
@@ -501,7 +511,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
             }
             __syncthreads();
         }
-        if (!bar_sync(A.bar, __LINE__)) return;
+        if (!bar_sync(A, __LINE__)) return;
 
         // ---- flexible GMRES cycles
         for (int cyc = 0; cyc < 1000; ++cyc) {
@@ -521,7 +531,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     row_fwd32<double, float, IN_V>(a, C.ln0, grp, smraw);
                     __syncthreads();
                 });
-                if (!bar_sync(A.bar, __LINE__)) return;
+                if (!bar_sync(A, __LINE__)) return;
                 if (blockIdx.x == 0 && tid == 0) A.flags[1 + ((j + 1) & 1)] = 0;
                 for_col_items(A, [&](int p, int tile) {
                     const EnsProb &P = A.prob[p];
@@ -530,7 +540,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     col32(col_args<float>(P, C, P.alpha + P.lam, P.k * P.chat, 1), C.ln1, tile, smraw);
                     __syncthreads();
                 });
-                if (!bar_sync(A.bar, __LINE__)) return;
+                if (!bar_sync(A, __LINE__)) return;
                 for_row_items(A, [&](int p, long long grp) {
                     const EnsProb &P = A.prob[p];
                     const EnsClass &C = A.cls[P.cls];
@@ -540,7 +550,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     row_inv32<double, float, OUT_APPLY>(a, C.ln0, grp, smraw);
                     __syncthreads();
                 });
-                if (!bar_sync(A.bar, __LINE__)) return;
+                if (!bar_sync(A, __LINE__)) return;
                 // w = A z_j in FP32 (stored FP64)
                 for_row_items(A, [&](int p, long long grp) {
                     const EnsProb &P = A.prob[p];
@@ -550,7 +560,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     row_fwd32<float, double, IN_V>(a, C.ln0, grp, smraw);
                     __syncthreads();
                 });
-                if (!bar_sync(A.bar, __LINE__)) return;
+                if (!bar_sync(A, __LINE__)) return;
                 for_col_items(A, [&](int p, int tile) {
                     const EnsProb &P = A.prob[p];
                     const EnsClass &C = A.cls[P.cls];
@@ -558,7 +568,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     col32(col_args<float>(P, C, P.alpha, P.k * P.chat, 0), C.ln1, tile, smraw);
                     __syncthreads();
                 });
-                if (!bar_sync(A.bar, __LINE__)) return;
+                if (!bar_sync(A, __LINE__)) return;
                 for_row_items(A, [&](int p, long long grp) {
                     const EnsProb &P = A.prob[p];
                     const EnsClass &C = A.cls[P.cls];
@@ -567,7 +577,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     row_inv32<float, double, OUT_MATVEC>(a, C.ln0, grp, smraw);
                     __syncthreads();
                 });
-                if (!bar_sync(A.bar, __LINE__)) return;
+                if (!bar_sync(A, __LINE__)) return;
                 // CGS2 in FP64, three passes; the block that completes a problem's chunks
                 // performs that problem's reduction (no separate reduce phases)
                 const int nv = j + 1;
@@ -586,7 +596,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     }
                     __syncthreads();
                 });
-                if (!bar_sync(A.bar, __LINE__)) return;
+                if (!bar_sync(A, __LINE__)) return;
                 // pass B: w <- w - V h1 ; h2 = V^T w
                 for_chunk_items(A, [&](int p, int ch) {
                     const EnsProb &P = A.prob[p];
@@ -605,7 +615,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     }
                     __syncthreads();
                 });
-                if (!bar_sync(A.bar, __LINE__)) return;
+                if (!bar_sync(A, __LINE__)) return;
                 // pass C: V_{j+1} = w - V h2 (unnormalised), ||V_{j+1}||^2, then the Hessenberg
                 // column, Givens rotation and stopping test by the completing block
                 for_chunk_items(A, [&](int p, int ch) {
@@ -657,7 +667,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     }
                     __syncthreads();
                 });
-                if (!bar_sync(A.bar, __LINE__)) return;
+                if (!bar_sync(A, __LINE__)) return;
                 if (*(volatile int *)cyc_flag == 0) break;
             }
             // ---- cycle end: y = H^{-1} g, x += Z y
@@ -673,7 +683,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                     s.cycles++;
                 }
             }
-            if (!bar_sync(A.bar, __LINE__)) return;
+            if (!bar_sync(A, __LINE__)) return;
             for_chunk_items(A, [&](int p, int ch) {
                 const EnsProb &P = A.prob[p];
                 if (!S[p].active) return;
@@ -686,7 +696,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                 ENS_NV(jd, (ens_xupdate<NVC>(P, lo, hi, ys)));
                 __syncthreads();
             });
-            if (!bar_sync(A.bar, __LINE__)) return;
+            if (!bar_sync(A, __LINE__)) return;
             // ---- FP64 true residual r = b - A x
             for_row_items(A, [&](int p, long long grp) {
                 const EnsProb &P = A.prob[p];
@@ -696,7 +706,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                 row_fwd_body<double, double, double, 8, IN_V>(a, grp, C.nthr_row, smraw);
                 __syncthreads();
             });
-            if (!bar_sync(A.bar, __LINE__)) return;
+            if (!bar_sync(A, __LINE__)) return;
             for_col_items(A, [&](int p, int tile) {
                 const EnsProb &P = A.prob[p];
                 const EnsClass &C = A.cls[P.cls];
@@ -704,7 +714,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                 col_dispatch<double>(col_args<double>(P, C, P.alpha, P.k * P.chat, 0), C.TW, tile, smraw);
                 __syncthreads();
             });
-            if (!bar_sync(A.bar, __LINE__)) return;
+            if (!bar_sync(A, __LINE__)) return;
             for_row_items(A, [&](int p, long long grp) {
                 const EnsProb &P = A.prob[p];
                 const EnsClass &C = A.cls[P.cls];
@@ -713,7 +723,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                 row_inv_body<double, double, double, 8, OUT_MATVEC>(a, grp, C.nthr_row, smraw);
                 __syncthreads();
             });
-            if (!bar_sync(A.bar, __LINE__)) return;
+            if (!bar_sync(A, __LINE__)) return;
             for_chunk_items(A, [&](int p, int ch) {
                 const EnsProb &P = A.prob[p];
                 if (!S[p].active) return;
@@ -730,7 +740,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                 __syncthreads();
             });
             if (blockIdx.x == 0 && tid == 0) { A.flags[0] = 0; A.flags[1] = 0; A.flags[2] = 0; }
-            if (!bar_sync(A.bar, __LINE__)) return;
+            if (!bar_sync(A, __LINE__)) return;
             for (int p = blockIdx.x; p < A.nprob; p += gridDim.x) {
                 if (!S[p].active) continue;
                 __shared__ double tot4[ENS_MAXM];
@@ -768,7 +778,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                 }
                 __syncthreads();
             }
-            if (!bar_sync(A.bar, __LINE__)) return;
+            if (!bar_sync(A, __LINE__)) return;
         }
         // ---- projected Euler update m <- (m + k v) / |m + k v|
         for (long long it = blockIdx.x; it < A.nchunks; it += gridDim.x) {
@@ -785,7 +795,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 4) ens_kernel(EnsArgs A) {
                 P.m[2 * P.N + q] = c / s;
             }
         }
-        if (!bar_sync(A.bar, __LINE__)) return;
+        if (!bar_sync(A, __LINE__)) return;
     }
 }
 
@@ -816,6 +826,8 @@ struct llg_ensemble {
     int graph_steps = -1;
     std::vector<int> caller;   // descriptor order -> caller's problem index
     std::string err;
+    long long budget = BARRIER_BUDGET;   // barrier wait limit (llg_ensemble_set_barrier_test)
+    int hold_block = -1;
 };
 
 namespace {
@@ -1021,6 +1033,15 @@ llg_status llg_ensemble_set_blocks(llg_ensemble *e, int blocks) {
     return LLG_OK;
 }
 
+llg_status llg_ensemble_set_barrier_test(llg_ensemble *e, long long budget_cycles, int hold_block) {
+    if (!e || budget_cycles < 0 || hold_block < -1) return LLG_ERR_INVALID_ARG;
+    e->budget = budget_cycles > 0 ? budget_cycles : BARRIER_BUDGET;
+    e->hold_block = hold_block;
+    if (e->gexec) { cudaGraphExecDestroy(e->gexec); e->gexec = nullptr; }   // the arguments changed
+    e->graph_steps = -1;
+    return LLG_OK;
+}
+
 int llg_ensemble_max_blocks(const llg_ensemble *e) {
     if (!e) return 0;
     int per_sm = 0, dev = 0, sms = 0;
@@ -1105,6 +1126,8 @@ llg_status llg_ensemble_run(llg_ensemble *e, int steps, llg_info *infos, int *us
     A.partB = e->partB;
     A.partC = e->partC;
     A.nchunks = e->nchunks;
+    A.budget = e->budget;
+    A.hold_block = e->hold_block;
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(e->blocks);
@@ -1152,6 +1175,12 @@ llg_status llg_ensemble_run(llg_ensemble *e, int steps, llg_info *infos, int *us
     if (used_graph) *used_graph = graph;
     if (hb.err) {
         e->err = "ensemble grid barrier gave up (blocks not co-resident?) at source line " + std::to_string(hb.where);
+        // a wait that gave up inside a phase can leave a last-block arrival counter raised
+        if (cudaMemsetAsync(e->cnt, 0, sizeof(unsigned) * e->nprob, e->stream) != cudaSuccess ||
+            cudaStreamSynchronize(e->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return LLG_ERR_CUDA;
+        }
         return LLG_ERR_TIMEOUT;
     }
     llg_status worst = LLG_OK;

@@ -13,6 +13,8 @@ Sec. 4.6 initial condition on (0, 2 pi)^3):
   * broadband    per component: random phases, amplitude |k|^-1.5 over all resolved integer
                  wavevectors k != 0, real part of the inverse transform, then per-node normalise
   * energy3d     (sin(x+z) cos(y+z), cos(x+z) cos(y+z), sin(y+z)) on (0, 2pi)^3 (unit length)
+  * ensemble_mix the batched workload: 32 problems each of 128^2, 256^2, 512^2 with seeded
+                 damping, time-step multiple and smooth/broadband field mix
 """
 from __future__ import annotations
 
@@ -121,3 +123,21 @@ def manufactured2d(n, t, alpha, c_ex=1.0):
     mxdm = np.stack([m[1] * dm[2] - m[2] * dm[1], m[2] * dm[0] - m[0] * dm[2], m[0] * dm[1] - m[1] * dm[0]])
     g = (alpha * dm + mxdm) / (1 + alpha ** 2) - c_ex * lap
     return m, g
+
+
+def ensemble_mix(seed=20260725, sizes=(128, 256, 512), per_size=32):
+    """The batched ensemble workload: for each grid size, `per_size` independent 2D problems
+    with alpha ~ U[0.01, 0.5], a time-step multiple c ~ U[2, 16] (the caller scales the
+    explicit exchange limit by it) and the field normalise(w smooth2d + (1 - w) broadband),
+    w ~ U[0, 1], both drawn with seed 1000 n + i.  Returns a list of (n, alpha, c, m0)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in sizes:
+        for i in range(per_size):
+            alpha = float(rng.uniform(0.01, 0.5))
+            c = float(rng.uniform(2.0, 16.0))
+            w = float(rng.uniform(0.0, 1.0))
+            s = 1000 * n + i
+            f = w * smooth2d((n, n), seed=s) + (1 - w) * broadband((n, n), seed=s)
+            out.append((n, alpha, c, _normalise(f)))
+    return out
