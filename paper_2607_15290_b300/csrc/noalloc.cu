@@ -12,15 +12,16 @@
 // until the process exits.  The caller still passes the inputs and the output.
 //
 // In host code the array's name is only a host-side stand-in, not a device
-// address, so on the first call on each device (with that device current) the
-// device address is fetched once with cudaGetSymbolAddress and cached; the kernels
-// get that address.  That first call should come before any stream capture.
+// address, so every call fetches the device address for the current device with
+// cudaGetSymbolAddress (which allocates nothing; a fetch per call also keeps a
+// device reset from leaving a stale address behind) and the kernels get that
+// address.  The first call on a device also loads the module there, so it should
+// come before any stream capture.
 // All calls share the array and it keeps the last call's contents: each call
 // rewrites the tables and clears the spectral region it uses, and calls that
 // overlap on the GPU (other streams or threads) race on it.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include "spectral_kernels.cuh"
 
 namespace {
@@ -36,30 +37,19 @@ constexpr long long SPEC_SLOTS = LLG_NOALLOC_MAX_SPECTRAL;
 
 static __device__ __align__(256) double2 g_noalloc_scratch[TABLE_SLOTS + SPEC_SLOTS];
 
-constexpr int MAX_DEVICES = 128;
-std::mutex g_mutex;
-double2 *g_ptr[MAX_DEVICES] = {};
-int g_sms[MAX_DEVICES] = {};
-
-// once per device, with that device current: the device address of the static array
+// with the device current: the device address of the static array and the SM count
 llg_status device_scratch(double2 **ptr, int *sms) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return LLG_ERR_CUDA; }
-    if (dev < 0 || dev >= MAX_DEVICES) return LLG_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) { cudaGetLastError(); return LLG_ERR_CUDA; }
-        int n = 0;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            return LLG_ERR_CUDA;
-        }
-        g_ptr[dev] = static_cast<double2 *>(p);
-        g_sms[dev] = n;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) { cudaGetLastError(); return LLG_ERR_CUDA; }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return LLG_ERR_CUDA;
     }
-    *ptr = g_ptr[dev];
-    *sms = g_sms[dev];
+    *ptr = static_cast<double2 *>(p);
+    *sms = n;
     return LLG_OK;
 }
 

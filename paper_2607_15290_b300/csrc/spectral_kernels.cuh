@@ -434,15 +434,20 @@ template <typename T> static inline ColPlan col_plan(int nl) {
 }
 
 // Dynamic shared-memory limit and the maximum shared-memory carveout, set once per
-// kernel (the carveout keeps shared memory from limiting the resident blocks).
+// kernel and device (the attributes apply to the current device only; the carveout keeps
+// shared memory from limiting the resident blocks).
 template <typename K> static inline cudaError_t set_smem(K kern, size_t bytes) {
     static thread_local const void *done[256];
+    static thread_local int done_dev[256];
     static thread_local int ndone = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
     for (int i = 0; i < ndone; ++i)
-        if (done[i] == (const void *)kern) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (done[i] == (const void *)kern && done_dev[i] == dev) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e == cudaSuccess && ndone < 256) done[ndone++] = (const void *)kern;
+    if (e == cudaSuccess && ndone < 256) { done[ndone] = (const void *)kern; done_dev[ndone] = dev; ++ndone; }
     (void)bytes;
     return e;
 }

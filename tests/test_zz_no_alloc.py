@@ -64,6 +64,28 @@ def test_noalloc_matches_context_apply_on_two_calls_in_a_row():
         ctx.close()
 
 
+# near the size limit (n1 * n2 * S up to LLG_NOALLOC_MAX_SPECTRAL = 262144), lines of up to
+# 1024 points in every axis position, both transpose modes: these FP64 row and column kernels
+# run only through this entry point (the context path takes compile-time-length kernels there)
+LARGE = [((512, 256), (1.0, 1.0)), ((1024, 128), (1.0, 0.5)), ((2, 1024), (0.25, 1.0)),
+         ((64, 64, 32), (1.0, 1.0, 2.0))]
+
+
+@pytest.mark.parametrize("n,Lc", LARGE, ids=["512x256", "1024x128", "2x1024", "64x64x32"])
+@pytest.mark.parametrize("transpose", [False, True], ids=["M", "MT"])
+def test_noalloc_matches_context_apply_near_the_size_limit(n, Lc, transpose):
+    prm = L.Params(alpha=0.15, k=2e-4, theta=0.5, lam=0.5)
+    m = torch.tensor(I.random_unit(n, seed=211), device="cuda")
+    p = torch.tensor(I.random_saddle_vector(n, seed=212), device="cuda")
+    z = _noalloc(n, Lc, prm, m, p, transpose)
+    ctx = L.Context(n, Lc)
+    ref = L.llg_ffthss_apply(ctx, prm, m, p, transpose=transpose)
+    torch.cuda.synchronize()
+    err = float((z - ref).abs().max() / ref.abs().max())
+    assert np.isfinite(err) and err <= 1e-12, (n, transpose, err)
+    ctx.close()
+
+
 def test_noalloc_refuses_grids_beyond_its_static_scratch():
     n = (1024, 1024)                       # needs 1024 * 1552 slots > LLG_NOALLOC_MAX_SPECTRAL
     prm = L.Params()
