@@ -304,6 +304,11 @@ def main():
     ap.add_argument("--midpoint-2d", action="store_true",
                     help="only the 1024^2 FP64 midpoint workload (20 steps, smooth and broadband fields): "
                          "iterations per solve, nodal drift, dissipation residual")
+    ap.add_argument("--gs-arith", default="f32x2", choices=["fp64", "f32x2"],
+                    help="arithmetic of the flexible solves' Gram-Schmidt passes: FP32 pairs on a "
+                         "planar-pair basis (default) or FP64 multiply-adds")
+    ap.add_argument("--pass-plan", default="five", choices=["five", "cluster"],
+                    help="3D FP32 round trips: five HBM passes, or x/y transforms in one cluster per plane")
     ap.add_argument("--n", type=int, default=128,
                     help="grid points per axis of the midpoint workload (128; smaller only for profiling captures)")
     args = ap.parse_args()
@@ -342,7 +347,9 @@ def main():
     N = n[0] * n[1] * n[2]
     ctx = L.Context(n)
     prm = L.Params(alpha=w["alpha"], k=w["k"], theta=0.5, lam=w["lam"], h_ext=w["h"])
-    opts = L.Opts(restart=30, rtol=1e-10, precision=L.PREC_FP32_FLEX, picard_tol=1e-10, picard_max=50)
+    gs = L.GS_F32X2 if args.gs_arith == "f32x2" else L.GS_FP64
+    opts = L.Opts(restart=30, rtol=1e-10, precision=L.PREC_FP32_FLEX, picard_tol=1e-10, picard_max=50, gs_arith=gs)
+    ctx.set_pass_plan(L.PLAN_CLUSTER if args.pass_plan == "cluster" else L.PLAN_FIVE)
     tuning = ctx.autotune()           # launch shapes of the axis passes, picked on this device
     m0 = torch.tensor(I.smooth3d(n), device="cuda")
     x = ctx.empty(4)
@@ -406,7 +413,18 @@ def main():
 
     # roofline of the profiled (dominant) kernel class
     avg_ms = prof["ms"] / max(prof["launches"], 1)
-    if args.roofline_class == "arnoldi":
+    if args.roofline_class == "arnoldi" and gs == L.GS_F32X2:
+        # FP32-pair passes: the FP64 unit is no longer the bound; the basis reads are
+        achieved = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "traffic_note": "not yet captured for the FP32-pair passes",
+                "algorithmic_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
+                "kernel": "arnoldi_pass_x2 (CGS2 multi-dot/update, FP64 data, FP32-pair arithmetic)",
+                "launches": prof["launches"], "avg_launch_ms": avg_ms,
+                "fp64_equivalent_tflops": prof["flops"] / (prof["ms"] / 1e3) / 1e12,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" + (" (fallback)" if pk.get("fallback") else "")}
+    elif args.roofline_class == "arnoldi":
         achieved = prof["flops"] / (prof["ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak, "traffic": ARNOLDI_TRAFFIC_BYTES if args.n == 128 else None,
@@ -424,11 +442,15 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (FP32 FFT-HSS + inner matvec, FP64 Arnoldi)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("f32+f64 (FP32 FFT-HSS + inner matvec; Gram-Schmidt in FP32-pair arithmetic on a basis whose "
+                  "first vector is FP64 and later ones FP32 pairs; FP64 least squares, true residual, update)"
+                  if gs == L.GS_F32X2 else "f32+f64 (FP32 FFT-HSS + inner matvec, FP64 Arnoldi)"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(n), "nodes": N, "unknowns": 4 * N, "alpha": w["alpha"],
                    "dt": w["k"], "dt_over_explicit_limit": 4.0, "lambda": w["lam"], "h_ext": list(w["h"]),
-                   "restart": 30, "rtol": 1e-10, "picard_tol": 1e-10,
+                   "restart": 30, "rtol": 1e-10, "picard_tol": 1e-10, "gram_schmidt": args.gs_arith,
+                   "pass_plan": args.pass_plan,
                    "l2": "inputs larger than L2 (fields 50-67 MB each, Krylov basis ~2 GB)",
                    "parallelism": f"replicas x{world} (independent problems, no collective)"},
         "solves_per_s": totals["solves"] / (ms / 1e3), "steps_per_s": totals["steps"] / (ms / 1e3),
@@ -613,6 +635,7 @@ def apply_sweep(args):
         n = (int(base),) * int(dim)
         N = int(np.prod(n))
         ctx = L.Context(n)
+        ctx.set_pass_plan(L.PLAN_CLUSTER if args.pass_plan == "cluster" else L.PLAN_FIVE)
         tuning = "" if args.no_autotune else ctx.autotune(fp64=args.precision == "fp64", fp32=args.precision == "fp32")
         f32 = args.precision == "fp32"
         dt = torch.float32 if f32 else torch.float64
@@ -633,7 +656,8 @@ def apply_sweep(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         w = 4 if f32 else 8
-        passes = 3 if len(n) == 2 else 5
+        # the cluster plan's grids (128^2 and 256^2 planes) make three passes of the FP32 apply
+        passes = 3 if len(n) == 2 or (args.pass_plan == "cluster" and f32 and n[0] == n[1] and n[0] in (128, 256)) else 5
         algo = (11 + 6 * (passes - 1)) * w * N
         out = {"grid": list(n), "precision": args.precision, "ms_per_apply": ms, "applies_per_s": 1e3 / ms,
                "gbs_algorithmic": algo / ms / 1e6, "frac_of_hbm": algo / ms / 1e6 / pk["hbm_gbs"],

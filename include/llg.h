@@ -52,6 +52,10 @@ enum { LLG_PREC_FP64 = 0, LLG_PREC_FP32_FLEX = 1 };
    (lambda I + S)^{-1} (lambda I + H)^{-1} of Sec. 3.2; the shifted symmetric part
    (lambda I + H)^{-1} alone (Algorithm 1 on the velocity, r / lambda on the multiplier); none */
 enum { LLG_PC_FFTHSS = 0, LLG_PC_HERMITIAN = 1, LLG_PC_NONE = 2 };
+/* arithmetic of the Gram--Schmidt passes (llg_opts.gs_arith) */
+enum { LLG_GS_FP64 = 0, LLG_GS_F32X2 = 1 };
+/* pass plan of 3D FP32 Fourier round trips (llg_set_pass_plan) */
+enum { LLG_PLAN_FIVE = 0, LLG_PLAN_CLUSTER = 1 };
 
 typedef struct llg_ctx llg_ctx;
 
@@ -96,6 +100,14 @@ typedef struct {
     int diagnostics;    /* steps: 1 = also compute energies and the dissipation residual */
     int preconditioner; /* forward solves: LLG_PC_FFTHSS (default), LLG_PC_HERMITIAN, LLG_PC_NONE;
                            transposed (adjoint) solves always use FFT--HSS */
+    int gs_arith;       /* arithmetic of the Gram--Schmidt passes of flexible solves (no counterpart
+                           in the paper): LLG_GS_FP64 = FP64 multiply-adds on FP64 data;
+                           LLG_GS_F32X2 = FP32-pair arithmetic (error-free FP32 products, Dekker
+                           1971, and two-sums, Knuth 4.2.2) on a basis whose vectors after the
+                           first are stored as planar FP32 pairs (about 47 significant bits), so
+                           the passes run on the FP32 pipes.  The first basis vector, the true
+                           residual, the Hessenberg least squares and the solution stay FP64.
+                           Used by FP32_FLEX solves with restart <= 32; other solves run FP64. */
 } llg_opts;
 
 typedef struct {
@@ -158,9 +170,10 @@ llg_status llg_ffthss_apply_f32(llg_ctx *ctx, const llg_params *prm, const float
    Same operation, layout and precision as llg_ffthss_apply (FP64; transpose != 0 applies
    M^{-T}); m, p, z are caller-owned device pointers; cuda_stream is a cudaStream_t (NULL =
    legacy default stream).  Grids beyond LLG_NOALLOC_MAX_SPECTRAL return
-   LLG_ERR_UNSUPPORTED_SIZE before any launch.  The first call on each device fetches the
-   array's device address (cudaGetSymbolAddress) with that device current; make that first
-   call before any stream capture.  All calls share the array (each rewrites its tables and
+   LLG_ERR_UNSUPPORTED_SIZE before any launch.  Every call fetches the array's device address
+   for the current device (cudaGetSymbolAddress, which allocates nothing), so nothing stale
+   survives a device reset; the first call on a device also loads the module there, so make
+   that first call before any stream capture.  All calls share the array (each rewrites its tables and
    clears the scratch it uses), so calls that overlap on the GPU -- on other streams or host
    threads -- race on it and must be serialised by the caller. */
 llg_status llg_ffthss_apply_noalloc(const llg_grid *grid, const llg_params *prm, const double *m,
@@ -259,6 +272,18 @@ llg_status llg_ensemble_set_barrier_test(llg_ensemble *ens, long long budget_cyc
 llg_status llg_ensemble_destroy(llg_ensemble *ens);
 const char *llg_ensemble_last_error(const llg_ensemble *ens);
 
+/* Pass plan of this context's 3D FP32 Fourier round trips (Algorithm 1's transforms and the
+   inner matvec of flexible GMRES; no counterpart in the paper).  LLG_PLAN_FIVE: x, y, z
+   (with the multiplier), y, x passes over HBM, 35 words per node for an FFT--HSS
+   application (the default).  LLG_PLAN_CLUSTER: the x and y transforms of each z-plane run
+   in one thread-block cluster that keeps the plane in its CTAs' shared memory (distributed
+   shared memory between them), so the spectrum crosses HBM only around the z pass, 23
+   words per node.  The cluster plan is compiled for 128 x 128 and 256 x 256 planes and the
+   FFT--HSS application (FP64 or FP32 input) and FP32 matvec; other grids and operators run
+   the five-pass plan either way.  Results agree to FP32 rounding.  INVALID_ARG for an
+   unknown plan. */
+llg_status llg_set_pass_plan(llg_ctx *ctx, int plan);
+
 /* Autotune the launch shapes of the Fourier axis passes for this context's grid (no
    counterpart in the paper): every compiled shape (register kernel with 4/8/16-column
    tiles; shared-memory-staged FP32 kernel with several tile/sub-batch sizes) is run on a
@@ -289,6 +314,14 @@ enum {
 llg_status llg_profile_begin(llg_ctx *ctx, int kernel_class);
 /* Stop timing, synchronise the stream and return the totals (HOST pointers, any may be NULL). */
 llg_status llg_profile_end(llg_ctx *ctx, double *total_ms, long long *launches, double *bytes, double *flops);
+/* Orthogonality of the Krylov basis of the context's last GMRES cycle (no counterpart in the
+   paper; a measurement of the Gram--Schmidt passes): *max_dev = max_{i,k} |delta_ik -
+   v_i . v_k| over the normalised stored vectors v_i = V_i / ||V_i||, each dot product in FP64;
+   *nvec the number of vectors compared (HOST pointers).  In a flexible solve the first stored
+   vector holds the final true residual once the solve has returned, so the comparison starts
+   at the second.  Synchronises the stream; allocates nvec^2 doubles.
+   Errors: INVALID_ARG (null pointer, no solve yet), OOM/CUDA. */
+llg_status llg_krylov_orthogonality(llg_ctx *ctx, double *max_dev, int *nvec);
 /* Measure the device's multiply-add rate with a register-resident FMA loop on the context's
    stream (fp64 != 0: double, else float); *tflops receives 2 * FMAs / s / 1e12 (HOST). */
 llg_status llg_probe_fma_rate(llg_ctx *ctx, int fp64, double *tflops);

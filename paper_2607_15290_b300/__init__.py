@@ -17,7 +17,7 @@ import ctypes as C
 from dataclasses import dataclass, field
 
 from . import _abi
-from ._abi import EX_FD2, EX_SPECTRAL, PC_FFTHSS, PC_HERMITIAN, PC_NONE, PREC_FP32_FLEX, PREC_FP64
+from ._abi import EX_FD2, EX_SPECTRAL, GS_F32X2, GS_FP64, PLAN_CLUSTER, PLAN_FIVE, PC_FFTHSS, PC_HERMITIAN, PC_NONE, PREC_FP32_FLEX, PREC_FP64
 
 __all__ = [
     "LLGError", "Params", "Opts", "Context", "EX_SPECTRAL", "EX_FD2", "PREC_FP64", "PREC_FP32_FLEX",
@@ -80,12 +80,13 @@ class Opts:
     picard_tol: float = 1e-10
     diagnostics: int = 0
     preconditioner: int = PC_FFTHSS
+    gs_arith: int = GS_FP64
 
     def c(self):
         o = _abi.Opts()
         o.restart, o.max_iters, o.rtol, o.precision = self.restart, self.max_iters, self.rtol, self.precision
         o.picard_max, o.picard_tol, o.diagnostics = self.picard_max, self.picard_tol, self.diagnostics
-        o.preconditioner = self.preconditioner
+        o.preconditioner, o.gs_arith = self.preconditioner, self.gs_arith
         return o
 
 
@@ -142,6 +143,16 @@ class Context:
         ms, n, by, fl = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
         self._check(self.lib.llg_profile_end(self.h, C.byref(ms), C.byref(n), C.byref(by), C.byref(fl)))
         return {"ms": ms.value, "launches": n.value, "bytes": by.value, "flops": fl.value}
+
+    def set_pass_plan(self, plan):
+        """PLAN_FIVE (default) or PLAN_CLUSTER for this context's 3D FP32 round trips."""
+        self._check(self.lib.llg_set_pass_plan(self.h, int(plan)))
+
+    def krylov_orthogonality(self):
+        """(max |I - V^T V|, vectors compared) for the basis of this context's last GMRES cycle."""
+        md, nv = C.c_double(), C.c_int()
+        self._check(self.lib.llg_krylov_orthogonality(self.h, C.byref(md), C.byref(nv)))
+        return md.value, nv.value
 
     def probe_fma_rate(self, fp64=True):
         """Measured multiply-add rate of this device in TFLOP/s (FP64 or FP32)."""

@@ -26,6 +26,8 @@ STATUS = {
 EX_SPECTRAL, EX_FD2 = 0, 1
 PREC_FP64, PREC_FP32_FLEX = 0, 1
 PC_FFTHSS, PC_HERMITIAN, PC_NONE = 0, 1, 2
+GS_FP64, GS_F32X2 = 0, 1
+PLAN_FIVE, PLAN_CLUSTER = 0, 1
 
 # every symbol the header declares, in declaration order
 EXPORTS = [
@@ -36,7 +38,8 @@ EXPORTS = [
     "llg_lower_order_field",
     "llg_ensemble_create", "llg_ensemble_run", "llg_ensemble_set_blocks", "llg_ensemble_max_blocks",
     "llg_ensemble_autotune", "llg_ensemble_set_barrier_test", "llg_ensemble_destroy", "llg_ensemble_last_error",
-    "llg_autotune", "llg_profile_begin", "llg_profile_end", "llg_probe_fma_rate", "llg_check_conversions",
+    "llg_set_pass_plan", "llg_autotune", "llg_profile_begin", "llg_profile_end", "llg_krylov_orthogonality", "llg_probe_fma_rate",
+    "llg_check_conversions",
 ]
 KCLASS = {"xfwd": 1, "axis": 2, "xinv": 3, "arnoldi": 4}
 
@@ -54,7 +57,7 @@ class Params(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("restart", C.c_int), ("max_iters", C.c_int), ("rtol", C.c_double), ("precision", C.c_int),
                 ("picard_max", C.c_int), ("picard_tol", C.c_double), ("diagnostics", C.c_int),
-                ("preconditioner", C.c_int)]
+                ("preconditioner", C.c_int), ("gs_arith", C.c_int)]
 
 
 class Problem(C.Structure):
@@ -106,6 +109,7 @@ def lib():
     L.llg_energy.argtypes = [ctx, P(Params), vp, d]
     L.llg_lower_order_field.argtypes = [ctx, P(Params), vp, vp]
     L.llg_autotune.argtypes = [ctx, C.c_int, C.c_char_p, C.c_int]
+    L.llg_set_pass_plan.argtypes = [ctx, C.c_int]
     L.llg_ensemble_create.argtypes = [P(Problem), C.c_int, P(Opts), vp, P(vp)]
     L.llg_ensemble_run.argtypes = [vp, C.c_int, P(Info), P(C.c_int)]
     L.llg_ensemble_set_blocks.argtypes = [vp, C.c_int]
@@ -117,6 +121,7 @@ def lib():
     L.llg_ensemble_last_error.restype = C.c_char_p
     L.llg_profile_begin.argtypes = [ctx, C.c_int]
     L.llg_profile_end.argtypes = [ctx, d, P(C.c_longlong), d, d]
+    L.llg_krylov_orthogonality.argtypes = [ctx, d, P(C.c_int)]
     L.llg_probe_fma_rate.argtypes = [ctx, C.c_int, d]
     L.llg_check_conversions.argtypes = [ctx, C.c_longlong, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     for name in EXPORTS:

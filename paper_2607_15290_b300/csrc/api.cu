@@ -23,6 +23,11 @@ llg_status set_error(llg_ctx *c, llg_status s, const std::string &msg) {
 }
 
 llg_status cuda_check(llg_ctx *c, cudaError_t e, const char *what) {
+    if (c->hprog && c->hprog[KERR_WORD]) {
+        // a kernel's bounded wait ran out (its block returned); the launch itself succeeded
+        c->hprog[KERR_WORD] = 0;
+        return set_error(c, LLG_ERR_TIMEOUT, std::string(what) + ": a bounded wait on an asynchronous copy ran out");
+    }
     if (e == cudaSuccess) return LLG_OK;
     cudaGetLastError();
     return set_error(c, e == cudaErrorMemoryAllocation ? LLG_ERR_OOM : LLG_ERR_CUDA,
@@ -162,8 +167,8 @@ __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, lo
 }
 
 // y = s a (s = *scale, or 1 when scale is NULL): the identity "preconditioner"
-template <typename TO>
-__global__ void k_scaled_copy(const double *__restrict__ a, const double *__restrict__ scale, TO *__restrict__ y,
+template <typename TO, typename TI>
+__global__ void k_scaled_copy(const TI *__restrict__ a, const double *__restrict__ scale, TO *__restrict__ y,
                               long long n) {
     const double sc = scale ? *scale : 1.0;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
@@ -350,6 +355,8 @@ llg_status check_opts(llg_ctx *c, const llg_opts *o) {
     if (o->picard_max < 1 || !(o->picard_tol > 0)) return set_error(c, LLG_ERR_INVALID_ARG, "need picard_max >= 1 and picard_tol > 0");
     if (o->preconditioner != LLG_PC_FFTHSS && o->preconditioner != LLG_PC_HERMITIAN && o->preconditioner != LLG_PC_NONE)
         return set_error(c, LLG_ERR_INVALID_ARG, "unknown preconditioner");
+    if (o->gs_arith != LLG_GS_FP64 && o->gs_arith != LLG_GS_F32X2)
+        return set_error(c, LLG_ERR_INVALID_ARG, "unknown Gram-Schmidt arithmetic");
     return LLG_OK;
 }
 
@@ -438,9 +445,9 @@ llg_status op_hermitian64(llg_ctx *c, const llg_params *p, double theta, const d
     return spectral_chain<double, double, double>(c, IN_V, OUT_APPLY, io, sym_shifted_inverse(c, p, theta));
 }
 
-template <typename TO>
-llg_status op_scaled_copy(llg_ctx *c, const double *x, const double *scale, TO *y) {
-    k_scaled_copy<TO><<<grid_blocks(c), RB_THREADS, 0, c->stream>>>(x, scale, y, 4 * c->geo.N);
+template <typename TO, typename TI = double>
+llg_status op_scaled_copy(llg_ctx *c, const TI *x, const double *scale, TO *y) {
+    k_scaled_copy<TO, TI><<<grid_blocks(c), RB_THREADS, 0, c->stream>>>(x, scale, y, 4 * c->geo.N);
     c->launches++;
     return cuda_check(c, cudaGetLastError(), "identity preconditioner");
 }
@@ -500,6 +507,19 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
             auto io = make_io<float, double, float>(m32, zz, ww, nullptr, p->lambda);
             io.skip = cyc;
             return spectral_chain<float, float, double>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
+        };
+        // the same two operators on FP32 data (FP32-pair Gram-Schmidt: hi planes of the basis and of w)
+        ops.fprec32 = [=](const float *xx, const double *s, float *zz) {
+            if (pc == LLG_PC_NONE) return op_scaled_copy<float, float>(c, xx, s, zz);
+            auto io = make_io<float, float, float>(m32, xx, zz, s, p->lambda);
+            io.plain_nodal = pc == LLG_PC_HERMITIAN;
+            io.skip = cyc;
+            return spectral_chain<float, float, float>(c, IN_V, OUT_APPLY, io, sym_shifted_inverse(c, p, theta));
+        };
+        ops.fmatvec32 = [=](const float *zz, float *ww) {
+            auto io = make_io<float, float, float>(m32, zz, ww, nullptr, p->lambda);
+            io.skip = cyc;
+            return spectral_chain<float, float, float>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
         };
     }
     return gmres_run(c, ops, flex, o, b, x, info, r0);
@@ -654,6 +674,7 @@ llg_status llg_create(const llg_grid *grid, void *cuda_stream, llg_ctx **out) {
             cudaHostGetDevicePointer((void **)&dp, hp, 0) == cudaSuccess) {
             memset(hp, 0, 64);
             c->hprog = static_cast<volatile int *>(hp);
+            c->dprog = dp;
             volatile int *dpv = dp;
             if ((e = cudaMemcpy(&c->gdev->prog, &dpv, sizeof(dpv), cudaMemcpyHostToDevice)) != cudaSuccess)
                 return fail(e, "GMRES progress words");
@@ -738,6 +759,19 @@ llg_status llg_profile_end(llg_ctx *c, double *total_ms, long long *launches, do
     if (bytes) *bytes = by;
     if (flops) *flops = fl;
     return LLG_OK;
+}
+
+llg_status llg_set_pass_plan(llg_ctx *c, int plan) {
+    LLG_GUARD(c);
+    if (plan != LLG_PLAN_FIVE && plan != LLG_PLAN_CLUSTER) return set_error(c, LLG_ERR_INVALID_ARG, "unknown pass plan");
+    c->pass_plan = plan;
+    return LLG_OK;
+}
+
+llg_status llg_krylov_orthogonality(llg_ctx *c, double *max_dev, int *nvec) {
+    LLG_GUARD(c);
+    if (!max_dev || !nvec) return set_error(c, LLG_ERR_INVALID_ARG, "null pointer");
+    return krylov_orthogonality(c, max_dev, nvec);
 }
 
 llg_status llg_probe_fma_rate(llg_ctx *c, int fp64, double *tflops) {

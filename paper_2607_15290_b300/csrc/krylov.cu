@@ -15,10 +15,12 @@
 // immediately.
 #include <cmath>
 #include <algorithm>
+#include <vector>
 #include "llg_internal.h"
 #include "krylov.h"
 #include "reduce.cuh"
 #include "convert.cuh"
+#include "f32pair.cuh"
 
 namespace llg {
 
@@ -195,6 +197,119 @@ __global__ void __launch_bounds__(RB_THREADS, MAXV <= 8 ? 2 : 1) arnoldi_pass_pi
     if (last_block_arrived(&gd->arrived)) arnoldi_finish(partials, gridDim.x, nv, gd, MODE, nv - 1);
 }
 
+// The three passes of a flexible solve with FP32-pair arithmetic (f32pair.cuh).  The
+// first basis vector V_0 is the FP64 true residual; every later basis vector and w are
+// planar FP32 pairs (a hi plane of n floats, then a lo plane, in the same 8 bytes per
+// value), so only V_0 is split on the integer pipes.  w as the FP32 inner matvec leaves
+// it is its hi plane alone (lo = 0); pass B writes w - V h1 as a pair, pass C writes
+// V_{j+1} as a pair.  Products and sums are error-free FP32 transformations; only the
+// per-thread totals return to FP64.  The FP64 unit is then out of the loop, and the
+// passes are bound by memory.  With PIPE, the next element's loads are issued before the
+// current element's arithmetic.
+template <int MAXV, int MODE, bool PIPE>
+__global__ void __launch_bounds__(RB_THREADS, MAXV <= 16 ? 2 : 1) arnoldi_pass_pair(const double *__restrict__ V, long long ldv,
+                                                                                     int nv, GmresDev *gd, const float *w_hi,
+                                                                                     const float *w_lo, float *o_hi, float *o_lo,
+                                                                                     long long n, double *__restrict__ partials) {
+    pdl_wait();
+    if (gd->done) return;
+    constexpr bool WLO = MODE == PASS_UPD_NRM;   // w carries a lo plane only after pass B
+    __shared__ f32x2 coef[MAXV];
+    if (threadIdx.x < nv) {
+        const double h = (MODE == PASS_UPD_DOT) ? gd->h1[threadIdx.x] : ((MODE == PASS_UPD_NRM) ? gd->h2[threadIdx.x] : 0.0);
+        coef[threadIdx.x] = split_f64(h * gd->scale[threadIdx.x]);
+    }
+    __syncthreads();
+    f32x2 acc[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) acc[i] = f32x2{0.0f, 0.0f};
+    long long lo, hi;
+    block_chunk(n, lo, hi);
+    const long long bd = blockDim.x;
+    struct Ld { double v0; float2 v[MAXV > 1 ? MAXV - 1 : 1]; float wh, wl; };
+    auto load = [&](Ld &d, long long e) {
+        if (e < hi) {
+            d.wh = w_hi[e];
+            d.wl = WLO ? w_lo[e] : 0.0f;
+            d.v0 = __ldg(&V[e]);
+#pragma unroll
+            for (int i = 1; i < MAXV; ++i) {
+                if (i < nv) {
+                    const float *b = reinterpret_cast<const float *>(V + i * ldv);
+                    d.v[i - 1] = make_float2(__ldg(&b[e]), __ldg(&b[n + e]));
+                }
+            }
+        }
+    };
+    auto work = [&](const Ld &d, long long e) {
+        if (e >= hi) return;
+        const f32x2 w{d.wh, d.wl};
+        f32x2 v[MAXV];
+        v[0] = split_f64(d.v0);
+#pragma unroll
+        for (int i = 1; i < MAXV; ++i)
+            if (i < nv) v[i] = f32x2{d.v[i - 1].x, d.v[i - 1].y};
+        if (MODE == PASS_DOT) {
+#pragma unroll
+            for (int i = 0; i < MAXV; ++i)
+                if (i < nv) fma_acc(v[i], w, acc[i]);
+        } else {
+            f32x2 u{0.0f, 0.0f};
+#pragma unroll
+            for (int i = 0; i < MAXV; ++i)
+                if (i < nv) fma_acc(coef[i], v[i], u);
+            const f32x2 wn = sub_pair(w, u);
+            o_hi[e] = wn.hi;
+            o_lo[e] = wn.lo;
+            if (MODE == PASS_UPD_DOT) {
+#pragma unroll
+                for (int i = 0; i < MAXV; ++i)
+                    if (i < nv) fma_acc(v[i], wn, acc[i]);
+            } else {
+                fma_acc(wn, wn, acc[0]);
+            }
+        }
+    };
+    if (PIPE) {
+        Ld a, b;
+        long long e = lo + threadIdx.x;
+        load(a, e);
+        for (; e < hi; e += 2 * bd) {
+            load(b, e + bd);
+            work(a, e);
+            load(a, e + 2 * bd);
+            work(b, e + bd);
+        }
+    } else {
+        for (long long e = lo + threadIdx.x; e < hi; e += bd) {
+            Ld d;
+            load(d, e);
+            work(d, e);
+        }
+    }
+    double accd[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) accd[i] = pair_to_f64(acc[i]);
+    block_reduce_store<MAXV>(accd, MODE == PASS_UPD_NRM ? 1 : nv, partials + (long long)blockIdx.x * RB_STRIDE);
+    if (last_block_arrived(&gd->arrived)) arnoldi_finish(partials, gridDim.x, nv, gd, MODE, nv - 1);
+}
+
+// partial sums of a . b over n values of two basis vectors, each FP64 or a planar FP32
+// pair (widened exactly), products and sums in FP64 (a measurement, not the hot path)
+__global__ void __launch_bounds__(RB_THREADS) dot_mixed_partials(const double *a, int a_pair, const double *b, int b_pair,
+                                                                 long long n, double *partials) {
+    double acc[1] = {0.0};
+    long long lo, hi;
+    block_chunk(n, lo, hi);
+    const float *ap = reinterpret_cast<const float *>(a), *bp = reinterpret_cast<const float *>(b);
+    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        const double x = a_pair ? f2d_exact(ap[e]) + f2d_exact(ap[n + e]) : a[e];
+        const double y = b_pair ? f2d_exact(bp[e]) + f2d_exact(bp[n + e]) : b[e];
+        acc[0] += x * y;
+    }
+    block_reduce_store<1>(acc, 1, partials + (long long)blockIdx.x * 64);
+}
+
 // start cycle `epoch`: beta = sqrt(red), g = beta e1, scale[0] = 1/beta, target = rel_factor * beta
 __global__ void cycle_init(GmresDev *gd, const double *red_dev, double rel_factor, int m, int epoch) {
     pdl_wait();
@@ -343,6 +458,38 @@ static void launch_pass(llg_ctx *c, int mode, const double *V, long long ldv, in
 #undef LLG_AP
 }
 
+template <int MAXV>
+static void launch_pass_pair(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const float *wh,
+                             const float *wl, float *oh, float *ol, long long n) {
+    GmresDev *gd = c->gdev;
+    constexpr bool pipe = MAXV <= 8;   // beyond 8 the second set of loads spills registers
+#define LLG_APP(KERN)                                                                                      \
+    {                                                                                                      \
+        auto k = KERN;                                                                                     \
+        const int nb = arnoldi_grid(c, k);                                                                 \
+        launch_pdl(k, dim3(nb), dim3(RB_THREADS), 0, c->stream, V, ldv, nv, gd, wh, wl, oh, ol, n, c->red); \
+        return;                                                                                            \
+    }
+    if (mode == PASS_DOT) LLG_APP((arnoldi_pass_pair<MAXV, PASS_DOT, pipe>))
+    if (mode == PASS_UPD_DOT) LLG_APP((arnoldi_pass_pair<MAXV, PASS_UPD_DOT, pipe>))
+    LLG_APP((arnoldi_pass_pair<MAXV, PASS_UPD_NRM, pipe>))
+#undef LLG_APP
+}
+
+// the pair passes are compiled for 1..32 basis vectors (restart <= 32)
+static void pass_dispatch_pair(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const float *wh,
+                               const float *wl, float *oh, float *ol, long long n) {
+#define LLG_NVP(K) case K: return launch_pass_pair<K>(c, mode, V, ldv, nv, wh, wl, oh, ol, n);
+    switch (nv) {
+        LLG_NVP(1) LLG_NVP(2) LLG_NVP(3) LLG_NVP(4) LLG_NVP(5) LLG_NVP(6) LLG_NVP(7) LLG_NVP(8)
+        LLG_NVP(9) LLG_NVP(10) LLG_NVP(11) LLG_NVP(12) LLG_NVP(13) LLG_NVP(14) LLG_NVP(15) LLG_NVP(16)
+        LLG_NVP(17) LLG_NVP(18) LLG_NVP(19) LLG_NVP(20) LLG_NVP(21) LLG_NVP(22) LLG_NVP(23) LLG_NVP(24)
+        LLG_NVP(25) LLG_NVP(26) LLG_NVP(27) LLG_NVP(28) LLG_NVP(29) LLG_NVP(30) LLG_NVP(31) LLG_NVP(32)
+        default: break;
+    }
+#undef LLG_NVP
+}
+
 static void pass_dispatch_raw(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const double *win, double *wout,
                               long long n) {
 #define LLG_NV(K) case K: return launch_pass<K>(c, mode, V, ldv, nv, win, wout, n);
@@ -360,18 +507,28 @@ static void pass_dispatch_raw(llg_ctx *c, int mode, const double *V, long long l
     else launch_pass<64>(c, mode, V, ldv, nv, win, wout, n);
 }
 
-// one Arnoldi step j on w = W (CGS2); writes the unnormalised V_{j+1}
-static llg_status arnoldi_step(llg_ctx *c, int j) {
+// one Arnoldi step j on w = W (CGS2); writes the unnormalised V_{j+1} (a planar FP32 pair
+// with `pairs`, where W holds the matvec's FP32 output in its hi plane)
+static llg_status arnoldi_step(llg_ctx *c, int j, bool pairs) {
     Workspace &w = c->ws;
     const long long n = w.n;
     const int nv = j + 1;
     // algorithmic bytes and flops of the three passes: (nv + 1) + 2 (nv + 2) words and
-    // nv + 2 nv + (nv + 1) multiply-adds per unknown; profiled as one interval of 3 launches
+    // nv + 2 nv + (nv + 1) multiply-adds per unknown (FP64 multiply-adds, or their FP32-pair
+    // equivalents); profiled as one interval of 3 launches
     const double nd = (double)n;
     prof_begin(c, K_ARNOLDI, 8.0 * nd * (3.0 * nv + 5.0), nd * (8.0 * nv + 2.0), j, 3);
-    pass_dispatch_raw(c, PASS_DOT, w.V, n, nv, w.W, nullptr, n);
-    pass_dispatch_raw(c, PASS_UPD_DOT, w.V, n, nv, w.W, w.W, n);
-    pass_dispatch_raw(c, PASS_UPD_NRM, w.V, n, nv, w.W, w.V + (long long)(j + 1) * n, n);
+    if (pairs) {
+        float *wh = reinterpret_cast<float *>(w.W), *wl = wh + n;
+        float *vh = reinterpret_cast<float *>(w.V + (long long)(j + 1) * n), *vl = vh + n;
+        pass_dispatch_pair(c, PASS_DOT, w.V, n, nv, wh, nullptr, nullptr, nullptr, n);
+        pass_dispatch_pair(c, PASS_UPD_DOT, w.V, n, nv, wh, nullptr, wh, wl, n);
+        pass_dispatch_pair(c, PASS_UPD_NRM, w.V, n, nv, wh, wl, vh, vl, n);
+    } else {
+        pass_dispatch_raw(c, PASS_DOT, w.V, n, nv, w.W, nullptr, n);
+        pass_dispatch_raw(c, PASS_UPD_DOT, w.V, n, nv, w.W, w.W, n);
+        pass_dispatch_raw(c, PASS_UPD_NRM, w.V, n, nv, w.W, w.V + (long long)(j + 1) * n, n);
+    }
     prof_end(c);
     c->launches += 3;
     return cuda_check(c, cudaGetLastError(), "arnoldi");
@@ -443,6 +600,9 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
     w.last_res = nullptr;
     const long long n = w.n;
     const int m = o->restart;
+    // FP32-pair Gram-Schmidt: flexible solves with at most 32 basis vectors
+    const bool pairs = flexible && o->gs_arith == LLG_GS_F32X2 && m <= 32 && ops.fprec32 && ops.fmatvec32;
+    w.pairs = pairs;
     double *dsc = c->dsc, *hsc = c->hsc;
     GmresDev *gh = static_cast<GmresDev *>(c->ghost);
 
@@ -507,13 +667,18 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
             double *vj = w.V + (long long)j * n;
             if (!flexible) {
                 st = ops.pop(vj, scale_j, w.W);
+            } else if (pairs) {
+                float *zj = w.Z + (long long)j * n;
+                // V_0 is FP64; V_j (j >= 1) a planar pair whose hi plane the FP32 preconditioner reads
+                st = j == 0 ? ops.fprec(vj, scale_j, zj) : ops.fprec32(reinterpret_cast<const float *>(vj), scale_j, zj);
+                if (st == LLG_OK) st = ops.fmatvec32(zj, reinterpret_cast<float *>(w.W));
             } else {
                 float *zj = w.Z + (long long)j * n;
                 st = ops.fprec(vj, scale_j, zj);
                 if (st == LLG_OK) st = ops.fmatvec(zj, w.W);
             }
             if (st != LLG_OK) return st;
-            if ((st = arnoldi_step(c, j)) != LLG_OK) return st;
+            if ((st = arnoldi_step(c, j, pairs)) != LLG_OK) return st;
             if (j + 1 == jmax) break;
             if (c->hprog) {
                 // keep one step queued behind the running one: wait for steps 0..j-1, stop once
@@ -557,6 +722,50 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
         else set_error(c, result, "GMRES breakdown (non-finite residual)");
     }
     return result;
+}
+
+// Orthogonality of the last GMRES cycle's basis: max_{i,k} |delta_ik - (s_i V_i).(s_k V_k)|
+// over the stored vectors (s_i the device-side scales), the dot products in FP64.  In a
+// flexible solve V_0 holds the final true residual once the solve has returned, so the
+// measurement starts at V_1 there.
+llg_status krylov_orthogonality(llg_ctx *c, double *max_dev, int *nvec) {
+    Workspace &w = c->ws;
+    if (!w.V) return set_error(c, LLG_ERR_INVALID_ARG, "no GMRES solve has run on this context");
+    GmresDev *gh = static_cast<GmresDev *>(c->ghost);
+    llg_status st = sync_read(c, gh, c->gdev, sizeof(GmresDev));
+    if (st != LLG_OK) return st;
+    const int first = w.last_res == w.V ? 1 : 0;
+    const int last = gh->jd;   // V_0 .. V_jd were written by the cycle
+    const int cnt = last - first + 1;
+    if (cnt < 1) return set_error(c, LLG_ERR_INVALID_ARG, "the last cycle stored no basis vector");
+    double *dots = nullptr;
+    cudaError_t e = cudaMalloc(&dots, sizeof(double) * cnt * cnt);
+    if (e != cudaSuccess) { cudaGetLastError(); return set_error(c, LLG_ERR_OOM, "orthogonality buffer"); }
+    const long long n = w.n;
+    const int nb = reduction_blocks(c);
+    for (int i = 0; i < cnt && st == LLG_OK; ++i)
+        for (int k = i; k < cnt; ++k) {
+            // in a solve with FP32-pair Gram-Schmidt every vector after V_0 is a planar pair
+            const int ia = first + i, ib = first + k;
+            launch_pdl(dot_mixed_partials, dim3(nb), dim3(RB_THREADS), 0, c->stream, (const double *)(w.V + (long long)ia * n),
+                       (int)(w.pairs && ia > 0), (const double *)(w.V + (long long)ib * n), (int)(w.pairs && ib > 0), n, c->red);
+            launch_pdl(sum_partials, dim3(1), dim3(RB_THREADS), 0, c->stream, (const double *)c->red, nb, dots + i * cnt + k);
+            c->launches += 2;
+        }
+    if (st == LLG_OK) st = cuda_check(c, cudaGetLastError(), "orthogonality");
+    std::vector<double> hd((size_t)cnt * cnt);
+    if (st == LLG_OK) st = sync_read(c, hd.data(), dots, sizeof(double) * cnt * cnt);
+    cudaFree(dots);
+    if (st != LLG_OK) return st;
+    double worst = 0.0;
+    for (int i = 0; i < cnt; ++i)
+        for (int k = i; k < cnt; ++k) {
+            const double g = hd[(size_t)i * cnt + k] * gh->scale[first + i] * gh->scale[first + k];
+            worst = std::max(worst, std::fabs((i == k ? 1.0 : 0.0) - g));
+        }
+    *max_dev = worst;
+    *nvec = cnt;
+    return LLG_OK;
 }
 
 }  // namespace llg

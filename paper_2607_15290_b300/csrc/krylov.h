@@ -41,6 +41,10 @@ struct SolveOps {
     // flexible GMRES: z = P(s x) stored FP32, then w = A z stored FP64
     std::function<llg_status(const double *x, const double *scale, float *z)> fprec;
     std::function<llg_status(const float *z, double *w)> fmatvec;
+    // flexible GMRES with FP32-pair Gram-Schmidt: z = P(s x) from an FP32 input (the hi plane
+    // of a planar-pair basis vector), and w = A z stored FP32 (the hi plane of w)
+    std::function<llg_status(const float *x, const double *scale, float *z)> fprec32;
+    std::function<llg_status(const float *z, float *w)> fmatvec32;
 };
 
 llg_status ensure_workspace(llg_ctx *c, int restart, bool flexible);
@@ -49,5 +53,8 @@ llg_status ensure_workspace(llg_ctx *c, int restart, bool flexible);
 // FP64 true residual b - A x (NULL when b = 0); it stays valid until the next solve.
 llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_opts *o, const double *b, double *x,
                      llg_info *info, const double *r0 = nullptr);
+
+// max |I - V^T V| over the last cycle's normalised basis vectors (HOST outputs)
+llg_status krylov_orthogonality(llg_ctx *c, double *max_dev, int *nvec);
 
 }  // namespace llg

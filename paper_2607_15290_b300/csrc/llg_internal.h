@@ -95,6 +95,10 @@ struct NodalIO {
     const int *skip;
 };
 
+// word of the host-mapped progress block that a kernel raises when one of its bounded
+// waits runs out (the host reports LLG_ERR_TIMEOUT at its next check)
+constexpr int KERR_WORD = 8;
+
 struct Workspace {
     int restart = 0;
     long long n = 0;          // 4 N
@@ -104,6 +108,7 @@ struct Workspace {
     double *T = nullptr;      // n
     double *R = nullptr;      // n
     const double *last_res = nullptr;   // final true residual of the last solve (T or V_0)
+    bool pairs = false;       // the last solve stored V_1.. and w as planar FP32 pairs
 };
 
 struct GmresDev;   // device-side Arnoldi state (krylov.cu)
@@ -112,6 +117,9 @@ struct GmresDev;   // device-side Arnoldi state (krylov.cu)
 // columns per block); kind 1 = staged kernel (TW = tile columns, CB = columns per
 // compute sub-batch, E = 8); kind 3 = FP32 register kernel with two adjacent columns
 // per thread (16-byte accesses; TW columns per tile)
+// launch shape of an axis pass: kind 0 register kernel (E points per thread, TW columns),
+// 1 staged tile (TW columns, CB per sub-batch), 3 two columns per thread, 4 persistent
+// kernel fed by the tensor memory accelerator (TW columns per tile)
 struct ColCfg {
     int kind, E, TW, CB;
 };
@@ -138,12 +146,14 @@ struct llg_ctx {
     llg::GmresDev *gdev = nullptr;
     void *ghost = nullptr;       // pinned host mirror of gdev
     volatile int *hprog = nullptr;   // host-mapped progress words of the running GMRES cycle
+    volatile int *dprog = nullptr;   // the same words as the device addresses them
     int cycle_epoch = 0;         // cycles started through this context
     llg::Workspace ws;
     float *m32 = nullptr;        // FP32 copy of the nodal field (mixed precision)
     double *aux = nullptr;       // 12 N doubles of stepper scratch
     int sm_count = 148;
     int sync_every = 4;          // blocking-poll interval when hprog is unavailable
+    int pass_plan = LLG_PLAN_FIVE;      // 3D FP32 round trips: LLG_PLAN_FIVE or LLG_PLAN_CLUSTER
     long long launches = 0;      // kernels launched through this context
     llg::ColCfg colcfg[2][llg::NSLOT];   // [FP32, FP64][slot] axis-pass shapes
     bool tuned[2] = {false, false};      // set by llg_autotune

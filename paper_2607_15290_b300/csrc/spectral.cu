@@ -21,6 +21,8 @@
 #include <algorithm>
 #include "spectral_kernels.cuh"
 #include "spectral_ct_launch.h"
+#include "spectral_xy.h"
+#include "col_tma.h"
 
 namespace llg {
 
@@ -122,7 +124,7 @@ static int ilog2_int(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 template <typename T> static int col_E(int nl) { return (sizeof(T) == 4 && nl >= 1024) ? 16 : (nl >= 8 ? 8 : nl); }
 
 // every launch shape the tuner may pick for a line length
-template <typename T> static std::vector<ColCfg> col_candidates(int nl) {
+template <typename T> static std::vector<ColCfg> col_candidates(const llg_ctx *c, int nl) {
     std::vector<ColCfg> v;
     const int E = col_E<T>(nl);
     const int tws[] = {4, 8, 16};
@@ -137,6 +139,10 @@ template <typename T> static std::vector<ColCfg> col_candidates(int nl) {
         // two adjacent columns per thread (16-byte accesses)
         for (int TW : {8, 16})
             if ((TW / 2) * (nl / E) <= 512) v.push_back({3, E, TW, 0});
+    }
+    if (sizeof(T) == 4 && tma::available(c, nl)) {
+        // persistent kernels fed by the tensor memory accelerator
+        for (int TW : {8, 16}) v.push_back({4, 8, TW, 0});
     }
     if (sizeof(T) == 4 && nl >= 64) {
         for (auto &sc : kStaged) {
@@ -158,6 +164,10 @@ template <typename T> static ColCfg col_default(int nl) {
 
 template <typename T>
 static cudaError_t launch_col_cfg(llg_ctx *c, int mode, const ColArgs<T> &a, int batches, const ColCfg &cfg) {
+    if (cfg.kind == 4) {
+        if constexpr (sizeof(T) == 4) return tma::col_launch(c, mode, a, batches, cfg.TW);
+        return cudaErrorInvalidValue;
+    }
     if (cfg.kind == 1) {
         if constexpr (sizeof(T) == 4) {
             if (ct::covers(a.logn)) return ct::staged(c, a.logn, mode, a, a.n0 + a.n0 / 2 + 1, batches, cfg.TW, cfg.CB);
@@ -213,6 +223,9 @@ static void slot_args(llg_ctx *c, int slot, const Symbol &sym, ColArgs<T> &ca, i
     }
 }
 
+// spectral columns that carry data (full spectrum of the packed pair + half spectrum)
+static double livec3(const SpecGeom &g) { return (double)(g.n[0] + g.n[0] / 2 + 1); }
+
 template <typename T, typename TIn, typename TOut>
 llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<TIn, TOut, T> &io,
                           const Symbol &sym) {
@@ -254,6 +267,32 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
     const double xf = fftf(1.5 * g.rows, n0, g.logn[0]);
 
     cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        if (c->pass_plan == LLG_PLAN_CLUSTER && xy::available(c, in_mode, out_mode)) {
+            // three passes: xy forward (cluster per plane), z, xy inverse
+            const double ylines = livec3(g) * g.n[2], zlines = livec3(g) * g.n[1];
+            prof_begin(c, K_XFWD, in_b + live * CB, xf + fftf(ylines, g.n[1], g.logn[1]));
+            e = xy::forward<TIn, TOut>(c, in_mode, ra);
+            prof_end(c);
+            if (e != cudaSuccess) return cuda_check(c, e, "xy-pass forward");
+            c->launches++;
+            ColArgs<T> ca{};
+            int batches = 1, mode = 7;
+            slot_args<T>(c, SLOT_Z, sym, ca, batches, mode);
+            ca.skip = io.skip;
+            prof_begin(c, K_AXIS, 2 * live * CB, 2 * fftf(zlines, g.n[2], g.logn[2]));
+            e = launch_col_cfg<T>(c, mode, ca, batches, slot_cfg<T>(c, SLOT_Z, ca.nl));
+            prof_end(c);
+            c->launches++;
+            if (e != cudaSuccess) return cuda_check(c, e, "z-pass");
+            prof_begin(c, K_XINV, live * CB + out_b, xf + fftf(ylines, g.n[1], g.logn[1]));
+            e = xy::inverse<TIn, TOut>(c, out_mode, ra);
+            prof_end(c);
+            if (e != cudaSuccess) return cuda_check(c, e, "xy-pass inverse");
+            c->launches++;
+            return LLG_OK;
+        }
+    }
 #define LLG_DISPATCH_E(FN, MODE)                                                              \
     switch (E) {                                                                              \
         case 2: e = FN<T, TIn, TOut, 2>(c, MODE, ra, blocks, threads, smr); break;            \
@@ -354,6 +393,7 @@ static std::string cfg_name(const ColCfg &f) {
     char b[64];
     if (f.kind == 0) snprintf(b, sizeof b, "register(E%d,TW%d)", f.E, f.TW);
     else if (f.kind == 3) snprintf(b, sizeof b, "paired(E%d,TW%d)", f.E, f.TW);
+    else if (f.kind == 4) snprintf(b, sizeof b, "tma(TW%d)", f.TW);
     else snprintf(b, sizeof b, "staged(TW%d,CB%d)", f.TW, f.CB);
     return b;
 }
@@ -403,7 +443,7 @@ static llg_status tune_prec(llg_ctx *c, std::string *report) {
         char line[256];
         snprintf(line, sizeof line, "%s slot %s (n=%d):", sizeof(T) == 4 ? "fp32" : "fp64", slot_names[slot], ca.nl);
         std::string rep = line;
-        for (const ColCfg &f : col_candidates<T>(ca.nl)) {
+        for (const ColCfg &f : col_candidates<T>(c, ca.nl)) {
             if ((e = run_once(f, nullptr)) != cudaSuccess) { cudaGetLastError(); rep += " " + cfg_name(f) + "=launch-fail"; continue; }
             k_live_maxdiff<C><<<512, 256, 0, c->stream>>>(ca.spec, ref, g.rows, g.S, live, part);
             cudaMemcpy(hp, part, sizeof(double) * 2 * 512, cudaMemcpyDeviceToHost);

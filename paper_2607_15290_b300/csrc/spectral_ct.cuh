@@ -24,8 +24,17 @@ template <int IN> struct InShape {
 // Block: G row pairs = 3G lines of P threads (line 3g: c1 + i c2 of row 2g, 3g+1:
 // of row 2g+1, 3g+2: c3 of rows 2g + i 2g+1).  Shared memory: two exchange
 // buffers of 3G padded lines.
-template <typename T, typename TIn, typename TOut, int LOGN, int IN>
-__device__ __forceinline__ void row_fwd_ct_body(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw) {
+// where the forward x-pass puts spectral value (row, col), row = 2 pair (+1) a global
+// spectral row: by default the spectrum in HBM
+template <typename C> struct SpecSink {
+    C *base;
+    long long S;
+    __device__ __forceinline__ void operator()(long long row, int col, C v) const { base[row * S + col] = v; }
+};
+
+template <typename T, typename TIn, typename TOut, int LOGN, int IN, class Sink>
+__device__ __forceinline__ void row_fwd_ct_body_to(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw,
+                                                   const Sink &sink) {
     using C = cplx<T>;
     using L = RowL<LOGN>;
     constexpr int N = 1 << LOGN, E = LineE<T, LOGN>::value, P = N / E, LS = L::size;
@@ -113,9 +122,8 @@ __device__ __forceinline__ void row_fwd_ct_body(const RowArgs<T, TIn, TOut> &a, 
     C *fb = (FreeBuf<LOGN, E, 0>::value ? buf1 : buf0) + line * LS;
     if (kind < 2) {
         if (valid) {
-            C *dst = a.spec + (2 * pair + kind) * (long long)a.S;
 #pragma unroll
-            for (int q = 0; q < E; ++q) dst[t + P * q] = v[q];
+            for (int q = 0; q < E; ++q) sink(2 * pair + kind, t + P * q, v[q]);
         }
     } else {
         const int b = L::template at<0>(t);
@@ -125,18 +133,21 @@ __device__ __forceinline__ void row_fwd_ct_body(const RowArgs<T, TIn, TOut> &a, 
     __syncthreads();
     if (kind == 2 && valid) {
         // U = FFT(c3[ya] + i c3[yb]);  C_a = (U_k + conj U_{-k}) / 2,  C_b = (U_k - conj U_{-k}) / (2i)
-        C *da = a.spec + (2 * pair) * (long long)a.S + N;
-        C *db = da + a.S;
 #pragma unroll
         for (int q = 0; q <= E / 2; ++q) {
             const int k = t + P * q;
             if (q == E / 2 && t > 0) break;
             const C uk = fb[L::template at<0>(k)];
             const C um = fb[L::template at<0>((N - k) & (N - 1))];
-            da[k] = cmk<C>((T)0.5 * (uk.x + um.x), (T)0.5 * (uk.y - um.y));
-            db[k] = cmk<C>((T)0.5 * (uk.y + um.y), (T)-0.5 * (uk.x - um.x));
+            sink(2 * pair, N + k, cmk<C>((T)0.5 * (uk.x + um.x), (T)0.5 * (uk.y - um.y)));
+            sink(2 * pair + 1, N + k, cmk<C>((T)0.5 * (uk.y + um.y), (T)-0.5 * (uk.x - um.x)));
         }
     }
+}
+
+template <typename T, typename TIn, typename TOut, int LOGN, int IN>
+__device__ __forceinline__ void row_fwd_ct_body(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw) {
+    row_fwd_ct_body_to<T, TIn, TOut, LOGN, IN>(a, bidx, smraw, SpecSink<cplx<T>>{a.spec, (long long)a.S});
 }
 
 template <typename T, typename TIn, typename TOut, int LOGN, int IN>
@@ -149,8 +160,11 @@ __global__ void __launch_bounds__(512) row_fwd_ct(RowArgs<T, TIn, TOut> a) {
 
 // ------------------------------------------------------------------ x-pass inverse
 
+// With `in` set, the spectrum of pair p is read from rows 2 (p - in_pair0) (+1) of `in`
+// (row stride in_S) instead of the global spectrum.
 template <typename T, typename TIn, typename TOut, int LOGN, int OUT>
-__device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw) {
+__device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw,
+                                                const cplx<T> *in = nullptr, long long in_pair0 = 0, int in_S = 0) {
     using C = cplx<T>;
     using L = RowL<LOGN>;
     constexpr int N = 1 << LOGN, E = LineE<T, LOGN>::value, P = N / E, LS = L::size, HN = N / 2;
@@ -165,16 +179,19 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
     const int gp = line / 3, kind = line - 3 * gp;
     const long long pair = pair0 + gp;
     const bool valid = gp < G && pair < npairs;
+    const C *const ibase = in ? in : a.spec;
+    const long long irow0 = in ? 2 * (pair - in_pair0) : 2 * pair;
+    const long long iS = in ? in_S : a.S;
     C v[E];
     if (valid) {
         if (kind < 2) {
-            const C *src = a.spec + (2 * pair + kind) * (long long)a.S;
+            const C *src = ibase + (irow0 + kind) * iS;
 #pragma unroll
             for (int q = 0; q < E; ++q) v[q] = src[t + P * q];
         } else {
             // full spectrum of c3[ya] + i c3[yb] from the two half spectra (Hermitian symmetry)
-            const C *sa = a.spec + (2 * pair) * (long long)a.S + N;
-            const C *sb = sa + a.S;
+            const C *sa = ibase + irow0 * iS + N;
+            const C *sb = sa + iS;
 #pragma unroll
             for (int q = 0; q < E; ++q) {
                 const int k = t + P * q;
