@@ -54,6 +54,10 @@ def peaks():
 ARNOLDI_TRAFFIC_BYTES = 371.3e6
 ARNOLDI_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 90 non-empty "
                         "arnoldi_pass launches of this workload (exact-count kernels, fused reduction)")
+# the same for the FP32-pair passes (arnoldi_pass_pair), 90 launches of this workload
+PAIR_TRAFFIC_BYTES = 394.5e6
+PAIR_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 90 arnoldi_pass_pair "
+                     "launches of this workload (profiles/gs_pass_pair_128cube_dram.md)")
 
 
 def aggregate_over_ranks(dist, ms, counts, device):
@@ -407,7 +411,7 @@ def main():
     pk = peaks()
     e2e = end_to_end(L, ctx, prm, opts, start_m, start_v, args.steps)
     if not args.no_extras and rank == 0:
-        extras = extras_leg(L, I, ctx, prm, w, m0, args)
+        extras = extras_leg(L, I, ctx, prm, w, m0, args, gs)
     fp64_peak = ctx.probe_fma_rate(True)
     fp32_peak = ctx.probe_fma_rate(False)
 
@@ -417,10 +421,10 @@ def main():
         # FP32-pair passes: the FP64 unit is no longer the bound; the basis reads are
         achieved = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                "traffic_note": "not yet captured for the FP32-pair passes",
+                "frac": achieved / pk["hbm_gbs"], "traffic": PAIR_TRAFFIC_BYTES if args.n == 128 else None,
+                "traffic_note": PAIR_TRAFFIC_NOTE,
                 "algorithmic_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
-                "kernel": "arnoldi_pass_x2 (CGS2 multi-dot/update, FP64 data, FP32-pair arithmetic)",
+                "kernel": "arnoldi_pass_pair (CGS2 multi-dot/update, FP32-pair arithmetic on a planar-pair basis)",
                 "launches": prof["launches"], "avg_launch_ms": avg_ms,
                 "fp64_equivalent_tflops": prof["flops"] / (prof["ms"] / 1e3) / 1e12,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" + (" (fallback)" if pk.get("fallback") else "")}
@@ -549,7 +553,7 @@ def cufft_apply_compare(L, I, ctx, prm, nn, ours_ms):
             "max_rel_diff_vs_ours": diff, "what": "torch.fft (cuFFT) R2C/C2R + unfused PyTorch elementwise nodal inverse"}
 
 
-def extras_leg(L, I, ctx, prm, w, m0, args):
+def extras_leg(L, I, ctx, prm, w, m0, args, gs):
     """FP32-flexible vs all-FP64 solve of one identical system and the isolated apply sweep.
     Runs after the timed region."""
     import torch
@@ -577,7 +581,7 @@ def extras_leg(L, I, ctx, prm, w, m0, args):
     L.llg_saddle_apply(ctx, prm, m0, x0, out=b)
     res = {}
     for name, prec in (("fp32flex", L.PREC_FP32_FLEX), ("fp64", L.PREC_FP64)):
-        o = L.Opts(restart=30, rtol=1e-10, precision=prec)
+        o = L.Opts(restart=30, rtol=1e-10, precision=prec, gs_arith=gs)
         times, its, rr, err = [], 0, 0.0, 0.0
         for rep in range(4):
             x = torch.zeros_like(b)
@@ -838,7 +842,8 @@ def ensemble_leg(args):
     steps = 5
     specs = [(n, alpha, c * 2 * alpha / ((1 + alpha ** 2) * 2 * (np.pi * n) ** 2), f)
              for n, alpha, c, f in I.ensemble_mix()]
-    opts = L.Opts(restart=30, rtol=1e-10, max_iters=900, precision=L.PREC_FP32_FLEX)
+    # the ensemble kernel's Gram-Schmidt passes are FP64; the one-at-a-time path runs the same
+    opts = L.Opts(restart=30, rtol=1e-10, max_iters=900, precision=L.PREC_FP32_FLEX, gs_arith=L.GS_FP64)
     stream = torch.cuda.Stream()
     probs = [{"n": (n, n), "params": L.Params(alpha=a, k=k, lam=0.5, h_ext=(0.0, 0.0, 0.5)),
               "m": torch.tensor(f, device="cuda"), "x": torch.zeros((4, n, n), dtype=torch.float64, device="cuda")}
@@ -881,6 +886,7 @@ def ensemble_leg(args):
     diff = max(float((p["m"] - s_).abs().max()) for p, s_ in zip(probs, seq))
     solves = len(specs) * steps
     out = {"leg": "ensemble", "problems": len(specs), "steps": steps, "grids": "32 x 128^2, 32 x 256^2, 32 x 512^2",
+           "gram_schmidt": "fp64",
            "ensemble_ms": ms_ens, "ensemble_solves_per_s": solves / (ms_ens / 1e3),
            "sequential_ms": ms_seq, "sequential_solves_per_s": solves / (ms_seq / 1e3),
            "speedup_vs_one_at_a_time": ms_seq / ms_ens, "persistent_blocks": blocks, "cuda_graph": used_graph,

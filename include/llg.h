@@ -105,8 +105,10 @@ typedef struct {
                            LLG_GS_F32X2 = FP32-pair arithmetic (error-free FP32 products, Dekker
                            1971, and two-sums, Knuth 4.2.2) on a basis whose vectors after the
                            first are stored as planar FP32 pairs (about 47 significant bits), so
-                           the passes run on the FP32 pipes.  The first basis vector, the true
-                           residual, the Hessenberg least squares and the solution stay FP64.
+                           the passes run on the FP32 pipes; the correction Z y of each cycle is
+                           summed the same way and added to the FP64 solution.  The first basis
+                           vector, the true residual, the Hessenberg least squares and the
+                           solution stay FP64.
                            Used by FP32_FLEX solves with restart <= 32; other solves run FP64. */
 } llg_opts;
 
@@ -245,7 +247,9 @@ typedef struct {
 } llg_problem;
 typedef struct llg_ensemble llg_ensemble;
 /* Allocate the per-problem workspace (Krylov bases, spectra) and descriptors.  opts: restart
-   (1..31), max_iters per solve, rtol (FP64 true residual); precision is always FP32-flexible.
+   (1..31), max_iters per solve, rtol (FP64 true residual); precision is always FP32-flexible,
+   and the Gram--Schmidt passes are always FP64 (gs_arith is ignored: in this kernel's
+   64-register budget the FP32-pair passes spill and ran slower).
    cuda_stream: a cudaStream_t (a non-default stream allows graph capture). */
 llg_status llg_ensemble_create(const llg_problem *probs, int count, const llg_opts *opts, void *cuda_stream,
                                llg_ensemble **out);

@@ -368,6 +368,24 @@ __global__ void __launch_bounds__(RB_THREADS) cycle_update(double *x, const TB *
     }
 }
 
+// x += Z y over an FP32 basis with FP32-pair arithmetic: each z value is exact in FP32, the
+// coefficient a pair, the products error-free and the per-element sum a two-sum chain; one
+// FP64 addition per element puts it into x (the FP64 form spends one FP64 multiply-add per
+// basis value, the bound of this pass)
+__global__ void __launch_bounds__(RB_THREADS) cycle_update_pair(double *x, const float *__restrict__ B, long long ldb,
+                                                                const GmresDev *__restrict__ gd, long long n) {
+    pdl_wait();
+    __shared__ f32x2 cf[64];
+    const int jd = gd->jd;
+    if (threadIdx.x < jd) cf[threadIdx.x] = split_f64(gd->coef[threadIdx.x]);
+    __syncthreads();
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        f32x2 s{0.0f, 0.0f};
+        for (int i = 0; i < jd; ++i) fma_acc(cf[i], f32x2{B[i * ldb + e], 0.0f}, s);
+        x[e] += pair_to_f64(s);
+    }
+}
+
 // out = b - t, partial sums of out^2
 __global__ void __launch_bounds__(RB_THREADS) residual_partials(const double *__restrict__ b, const double *t,
                                                                 double *out, long long n, double *partials) {
@@ -462,7 +480,10 @@ template <int MAXV>
 static void launch_pass_pair(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const float *wh,
                              const float *wl, float *oh, float *ol, long long n) {
     GmresDev *gd = c->gdev;
-    constexpr bool pipe = MAXV <= 8;   // beyond 8 the second set of loads spills registers
+    // passes A and C (one multiply-add term per loaded value) load the next element ahead;
+    // pass B, with two terms per value, runs at higher occupancy instead (beyond 8 vectors the
+    // second set of loads would spill registers anyway)
+    constexpr bool pipe = MAXV <= 8;
 #define LLG_APP(KERN)                                                                                      \
     {                                                                                                      \
         auto k = KERN;                                                                                     \
@@ -471,7 +492,7 @@ static void launch_pass_pair(llg_ctx *c, int mode, const double *V, long long ld
         return;                                                                                            \
     }
     if (mode == PASS_DOT) LLG_APP((arnoldi_pass_pair<MAXV, PASS_DOT, pipe>))
-    if (mode == PASS_UPD_DOT) LLG_APP((arnoldi_pass_pair<MAXV, PASS_UPD_DOT, pipe>))
+    if (mode == PASS_UPD_DOT) LLG_APP((arnoldi_pass_pair<MAXV, PASS_UPD_DOT, false>))
     LLG_APP((arnoldi_pass_pair<MAXV, PASS_UPD_NRM, pipe>))
 #undef LLG_APP
 }
@@ -694,7 +715,10 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
         }
         launch_pdl(cycle_backsolve, dim3(1), dim3(32), 0, c->stream, c->gdev, flexible ? 1 : 0);
         const int ub = reduction_blocks(c) * 2;
-        if (flexible)
+        if (flexible && pairs)
+            launch_pdl(cycle_update_pair, dim3(ub), dim3(RB_THREADS), 0, c->stream, x, (const float *)w.Z, n,
+                       (const GmresDev *)c->gdev, n);
+        else if (flexible)
             launch_pdl(cycle_update<float>, dim3(ub), dim3(RB_THREADS), 0, c->stream, x, w.Z, n, c->gdev, n);
         else
             launch_pdl(cycle_update<double>, dim3(ub), dim3(RB_THREADS), 0, c->stream, x, w.V, n, c->gdev, n);
