@@ -1,0 +1,203 @@
+// gs_tma.cu -- the Gram--Schmidt passes of flexible solves in FP32-pair arithmetic (the same
+// arithmetic and data layout as arnoldi_pass_pair in krylov.cu), with their operands staged
+// in shared memory by bulk copies.
+//
+// Each persistent block walks its share of the vectors in chunks through a two-stage ring:
+// while it computes on chunk k from shared memory, the bulk copies of chunk k+1 (the FP32
+// hi plane of w, in pass C also its lo plane, the FP64 first basis vector and the hi and lo
+// planes of every later one; cp.async.bulk, completion on an mbarrier) are in flight.  The
+// loads then no longer hold registers while they wait, so the block keeps many bytes in
+// flight at any occupancy; the register form of these passes waits on its loads (long-
+// scoreboard stalls) at 56-70% of the memory floor.
+//
+// Every mbarrier wait is bounded (about 1 s of clock).  A wait that runs out raises the
+// error word in host-mapped memory (the host reports LLG_ERR_TIMEOUT at its next check),
+// waits (bounded) for the block's copies in flight, and the block still stores its partial
+// sums and counts its arrival, so the pass's last-block bookkeeping stays consistent.
+#include <algorithm>
+#include "spectral_kernels.cuh"
+#include "krylov_dev.cuh"
+#include "f32pair.cuh"
+#include "tma_ptx.cuh"
+#include "gs_tma.h"
+
+namespace llg {
+namespace gst {
+
+using namespace llg::tma;
+
+constexpr int NT = 256;                  // threads per block
+constexpr int STAGE_TARGET = 48 * 1024;  // bytes per stage (two stages per block)
+
+// bytes staged per vector element: w hi (+ w lo in pass C), V_0 (FP64), 8 per later vector
+__host__ __device__ constexpr int elem_bytes(int nv, int mode) { return 4 + (mode == PASS_UPD_NRM ? 4 : 0) + 8 * nv; }
+
+// chunk layout in a stage: [w hi][w lo (pass C)][V_0][V_1 hi][V_1 lo] ... each CH long
+struct ChunkLayout {
+    int CH;
+    __host__ __device__ size_t stage_bytes(int nv, int mode) const {
+        return ((size_t)CH * elem_bytes(nv, mode) + 127) / 128 * 128;
+    }
+};
+
+template <int MAXV, int MODE>
+__global__ void __launch_bounds__(NT, 2) gs_pass_staged(const double *__restrict__ V, long long ldv, int nv, GmresDev *gd,
+                                                      const float *w_hi, const float *w_lo, float *o_hi, float *o_lo,
+                                                      long long n, ChunkLayout lay, double *__restrict__ partials,
+                                                      volatile int *err) {
+    pdl_wait();
+    if (gd->done) return;
+    constexpr bool WLO = MODE == PASS_UPD_NRM;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    unsigned char *ring = smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u);
+    __shared__ __align__(8) unsigned long long bar[2];
+    __shared__ int s_ok;
+    __shared__ f32x2 coef[MAXV];
+    const int tid = threadIdx.x;
+    const int CH = lay.CH;
+    const size_t SB = lay.stage_bytes(nv, MODE);
+    if (tid < nv) {
+        const double h = (MODE == PASS_UPD_DOT) ? gd->h1[tid] : ((MODE == PASS_UPD_NRM) ? gd->h2[tid] : 0.0);
+        coef[tid] = split_f64(h * gd->scale[tid]);
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const long long nchunks = (n + CH - 1) / CH;
+    // stage pointers
+    auto w_h_s = [&](int st) { return reinterpret_cast<float *>(ring + st * SB); };
+    auto w_l_s = [&](int st) { return w_h_s(st) + CH; };
+    auto v0_s = [&](int st) { return reinterpret_cast<double *>(w_h_s(st) + (WLO ? 2 : 1) * CH); };
+    auto vh_s = [&](int st, int i) { return reinterpret_cast<float *>(v0_s(st) + CH) + (size_t)2 * (i - 1) * CH; };
+    auto issue = [&](long long chunk, int st) {
+        const long long e0 = chunk * CH;
+        const unsigned len = (unsigned)std::min<long long>(CH, n - e0);
+        mbar_expect_tx(&bar[st], len * (unsigned)elem_bytes(nv, MODE));
+        bulk_load(w_h_s(st), w_hi + e0, len * 4u, &bar[st]);
+        if (WLO) bulk_load(w_l_s(st), w_lo + e0, len * 4u, &bar[st]);
+        bulk_load(v0_s(st), V + e0, len * 8u, &bar[st]);
+        for (int i = 1; i < nv; ++i) {
+            const float *b = reinterpret_cast<const float *>(V + i * ldv);
+            bulk_load(vh_s(st, i), b + e0, len * 4u, &bar[st]);
+            bulk_load(vh_s(st, i) + CH, b + n + e0, len * 4u, &bar[st]);
+        }
+    };
+    f32x2 acc[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) acc[i] = f32x2{0.0f, 0.0f};
+    const long long first = blockIdx.x, stride = gridDim.x;
+    if (tid == 0 && first < nchunks) issue(first, 0);
+    bool failed = false;
+    int k = 0;
+    for (long long chunk = first; chunk < nchunks; chunk += stride, ++k) {
+        const int st = k & 1;
+        const unsigned parity = (unsigned)((k >> 1) & 1);
+        if (tid == 0) {
+            // the other stage was last read in iteration k - 1, which every thread has left
+            if (chunk + stride < nchunks) issue(chunk + stride, st ^ 1);
+            s_ok = mbar_wait_bounded(&bar[st], parity) ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) { failed = true; break; }
+        if (__syncthreads_or(mbar_wait_bounded(&bar[st], parity) ? 0 : 1)) { failed = true; break; }
+        const long long e0 = chunk * CH;
+        const int len = (int)std::min<long long>(CH, n - e0);
+        const float *wh = w_h_s(st), *wl = w_l_s(st);
+        const double *v0 = v0_s(st);
+        for (int r = tid; r < len; r += NT) {
+            const f32x2 w{wh[r], WLO ? wl[r] : 0.0f};
+            f32x2 v[MAXV];
+            v[0] = split_f64(v0[r]);
+#pragma unroll
+            for (int i = 1; i < MAXV; ++i)
+                if (i < nv) {
+                    const float *b = vh_s(st, i);
+                    v[i] = f32x2{b[r], b[CH + r]};
+                }
+            if (MODE == PASS_DOT) {
+#pragma unroll
+                for (int i = 0; i < MAXV; ++i)
+                    if (i < nv) fma_acc(v[i], w, acc[i]);
+            } else {
+                f32x2 u{0.0f, 0.0f};
+#pragma unroll
+                for (int i = 0; i < MAXV; ++i)
+                    if (i < nv) fma_acc(coef[i], v[i], u);
+                const f32x2 wn = sub_pair(w, u);
+                o_hi[e0 + r] = wn.hi;
+                o_lo[e0 + r] = wn.lo;
+                if (MODE == PASS_UPD_DOT) {
+#pragma unroll
+                    for (int i = 0; i < MAXV; ++i)
+                        if (i < nv) fma_acc(v[i], wn, acc[i]);
+                } else {
+                    fma_acc(wn, wn, acc[0]);
+                }
+            }
+        }
+        __syncthreads();   // this stage is free for the copies of chunk k + 2
+    }
+    if (failed && tid == 0) {
+        *err = 1;
+        __threadfence_system();
+        // copies still in flight land in this block's shared memory: wait for them (bounded)
+        for (int q = 0; q < 2; ++q) {
+            const long long c = first + (long long)(k + q) * stride;
+            if (c < nchunks) mbar_wait_bounded(&bar[(k + q) & 1], (unsigned)(((k + q) >> 1) & 1));
+        }
+    }
+    double accd[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) accd[i] = failed ? 0.0 : pair_to_f64(acc[i]);
+    block_reduce_store<MAXV>(accd, MODE == PASS_UPD_NRM ? 1 : nv, partials + (long long)blockIdx.x * RB_STRIDE);
+    if (last_block_arrived(&gd->arrived)) arnoldi_finish(partials, gridDim.x, nv, gd, MODE, nv - 1);
+}
+
+template <int MAXV, int MODE>
+static cudaError_t launch_one(llg_ctx *c, const double *V, long long ldv, int nv, const float *wh, const float *wl,
+                              float *oh, float *ol, long long n) {
+    ChunkLayout lay;
+    lay.CH = std::max(4, (STAGE_TARGET / elem_bytes(nv, MODE)) / 4 * 4);
+    if (lay.CH > n) lay.CH = (int)((n + 3) / 4 * 4);
+    const size_t sm = 2 * lay.stage_bytes(nv, MODE) + 128;
+    auto k = gs_pass_staged<MAXV, MODE>;
+    cudaError_t e = set_smem(k, sm);
+    if (e != cudaSuccess) return e;
+    int per = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, NT, sm)) != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    const long long nchunks = (n + lay.CH - 1) / lay.CH;
+    const int blocks = (int)std::min<long long>(nchunks, std::min(per * c->sm_count, partial_capacity(c)));
+    return launch_pdl(k, dim3(blocks), dim3(NT), sm, c->stream, V, ldv, nv, c->gdev, wh, wl, oh, ol, n, lay, c->red,
+                      c->dprog + KERR_WORD);
+}
+
+template <int MAXV>
+static cudaError_t launch_nv(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const float *wh,
+                             const float *wl, float *oh, float *ol, long long n) {
+    if (mode == PASS_DOT) return launch_one<MAXV, PASS_DOT>(c, V, ldv, nv, wh, wl, oh, ol, n);
+    if (mode == PASS_UPD_DOT) return launch_one<MAXV, PASS_UPD_DOT>(c, V, ldv, nv, wh, wl, oh, ol, n);
+    return launch_one<MAXV, PASS_UPD_NRM>(c, V, ldv, nv, wh, wl, oh, ol, n);
+}
+
+bool available(const llg_ctx *c, long long n) { return c->dprog != nullptr && n % 4 == 0; }
+
+cudaError_t pass(llg_ctx *c, int mode, const double *V, long long ldv, int nv, const float *wh, const float *wl,
+                 float *oh, float *ol, long long n) {
+#define LLG_GSN(K) case K: return launch_nv<K>(c, mode, V, ldv, nv, wh, wl, oh, ol, n);
+    switch (nv) {
+        LLG_GSN(1) LLG_GSN(2) LLG_GSN(3) LLG_GSN(4) LLG_GSN(5) LLG_GSN(6) LLG_GSN(7) LLG_GSN(8)
+        LLG_GSN(9) LLG_GSN(10) LLG_GSN(11) LLG_GSN(12) LLG_GSN(13) LLG_GSN(14) LLG_GSN(15) LLG_GSN(16)
+        LLG_GSN(17) LLG_GSN(18) LLG_GSN(19) LLG_GSN(20) LLG_GSN(21) LLG_GSN(22) LLG_GSN(23) LLG_GSN(24)
+        LLG_GSN(25) LLG_GSN(26) LLG_GSN(27) LLG_GSN(28) LLG_GSN(29) LLG_GSN(30) LLG_GSN(31) LLG_GSN(32)
+        default: break;
+    }
+#undef LLG_GSN
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gst
+}  // namespace llg

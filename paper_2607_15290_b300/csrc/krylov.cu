@@ -21,6 +21,8 @@
 #include "reduce.cuh"
 #include "convert.cuh"
 #include "f32pair.cuh"
+#include "krylov_dev.cuh"
+#include "gs_tma.h"
 
 namespace llg {
 
@@ -28,70 +30,6 @@ int reduction_blocks(llg_ctx *c) { return 2 * c->sm_count; }
 int partial_capacity(llg_ctx *c) { return 8 * c->sm_count; }
 
 // ------------------------------------------------------------------ Arnoldi passes
-
-enum { PASS_DOT = 0, PASS_UPD_DOT = 1, PASS_UPD_NRM = 2 };
-
-// Finish of Arnoldi pass `mode` of step j, run by the block that completes the pass
-// last: sums the per-block partials in a fixed order, then
-//   mode 0: h1 = scale .* sums;  mode 1: h2 = scale .* sums;
-//   mode 2: ||w||^2 -> Hessenberg column h1 + h2 and h_{j+1,j}, previous Givens
-//           rotations applied, new rotation, residual estimate, stopping flag.
-// The state the sequential part needs is first gathered into shared memory by all
-// threads, so the single-thread part runs on shared memory, not on a chain of
-// dependent global loads.
-__device__ __noinline__ void arnoldi_finish(const double *partials, int nb, int nv, GmresDev *gd, int mode, int j) {
-    __shared__ double tot[64];
-    __shared__ double col[GmresDev::LD + 1], cs_s[GmresDev::MAXM], sn_s[GmresDev::MAXM];
-    __shared__ double gj;
-    block_sum_partials_l2(partials, nb, mode == PASS_UPD_NRM ? 1 : nv, tot);
-    __syncthreads();
-    if (mode != PASS_UPD_NRM) {
-        double *h = mode == PASS_DOT ? gd->h1 : gd->h2;
-        for (int i = threadIdx.x; i < nv; i += blockDim.x) h[i] = tot[i] * gd->scale[i];
-        return;
-    }
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = gd->h1[i] + gd->h2[i];
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
-        cs_s[i] = gd->cs[i];
-        sn_s[i] = gd->sn[i];
-    }
-    if (threadIdx.x == 0) gj = gd->g[j];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double hn = sqrt(tot[0]);
-        col[j + 1] = hn;
-        for (int i = 0; i < j; ++i) {
-            const double a = col[i], b = col[i + 1];
-            col[i] = cs_s[i] * a + sn_s[i] * b;
-            col[i + 1] = -sn_s[i] * a + cs_s[i] * b;
-        }
-        const double a = col[j], b = col[j + 1];
-        const double rr = hypot(a, b);
-        const double cs = rr > 0.0 ? a / rr : 1.0, sn = rr > 0.0 ? b / rr : 0.0;
-        col[j] = rr;
-        col[j + 1] = 0.0;
-        gd->cs[j] = cs;
-        gd->sn[j] = sn;
-        gd->scale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-        gd->g[j + 1] = -sn * gj;
-        gd->g[j] = cs * gj;
-        gd->jd = j + 1;
-        const double est = fabs(sn * gj);
-        if (!isfinite(est) || !isfinite(hn)) {
-            gd->breakdown = 1;
-            gd->done = 1;
-        } else if (est <= gd->target || hn == 0.0) {
-            gd->done = 1;
-        }
-        if (gd->prog) {
-            gd->prog[1] = j + 1;
-            gd->prog[2] = gd->done;
-            __threadfence_system();
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) gd->H[i + GmresDev::LD * j] = col[i];
-}
 
 template <int MAXV, int MODE>
 __global__ void __launch_bounds__(RB_THREADS) arnoldi_pass(const double *__restrict__ V, long long ldv, int nv,
@@ -542,9 +480,17 @@ static llg_status arnoldi_step(llg_ctx *c, int j, bool pairs) {
     if (pairs) {
         float *wh = reinterpret_cast<float *>(w.W), *wl = wh + n;
         float *vh = reinterpret_cast<float *>(w.V + (long long)(j + 1) * n), *vl = vh + n;
-        pass_dispatch_pair(c, PASS_DOT, w.V, n, nv, wh, nullptr, nullptr, nullptr, n);
-        pass_dispatch_pair(c, PASS_UPD_DOT, w.V, n, nv, wh, nullptr, wh, wl, n);
-        pass_dispatch_pair(c, PASS_UPD_NRM, w.V, n, nv, wh, wl, vh, vl, n);
+        if (gst::available(c, n)) {
+            // operands staged in shared memory by bulk copies
+            cudaError_t e = gst::pass(c, PASS_DOT, w.V, n, nv, wh, nullptr, nullptr, nullptr, n);
+            if (e == cudaSuccess) e = gst::pass(c, PASS_UPD_DOT, w.V, n, nv, wh, nullptr, wh, wl, n);
+            if (e == cudaSuccess) e = gst::pass(c, PASS_UPD_NRM, w.V, n, nv, wh, wl, vh, vl, n);
+            if (e != cudaSuccess) { prof_end(c); return cuda_check(c, e, "Gram-Schmidt pass"); }
+        } else {
+            pass_dispatch_pair(c, PASS_DOT, w.V, n, nv, wh, nullptr, nullptr, nullptr, n);
+            pass_dispatch_pair(c, PASS_UPD_DOT, w.V, n, nv, wh, nullptr, wh, wl, n);
+            pass_dispatch_pair(c, PASS_UPD_NRM, w.V, n, nv, wh, wl, vh, vl, n);
+        }
     } else {
         pass_dispatch_raw(c, PASS_DOT, w.V, n, nv, w.W, nullptr, n);
         pass_dispatch_raw(c, PASS_UPD_DOT, w.V, n, nv, w.W, w.W, n);
