@@ -284,6 +284,22 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def dtype_string(gs, ch):
+    """the arithmetic the timed step computes in"""
+    import paper_2607_15290_b300 as L
+    parts = ["FP32 FFT-HSS + inner matvec"]
+    if gs == L.GS_F32X2:
+        parts.append("Gram-Schmidt in FP32-pair arithmetic on a basis whose first vector is FP64 and later ones FP32 pairs")
+    else:
+        parts.append("FP64 Gram-Schmidt")
+    if ch == L.CHAIN_F32X2:
+        parts.append("true residuals and right-hand side through FP32-pair Fourier chains (FP64 in and out)")
+    else:
+        parts.append("FP64 true residuals and right-hand side")
+    parts.append("FP64 least squares and update")
+    return "f32+f64 (" + "; ".join(parts) + ")"
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -311,6 +327,9 @@ def main():
     ap.add_argument("--gs-arith", default="f32x2", choices=["fp64", "f32x2"],
                     help="arithmetic of the flexible solves' Gram-Schmidt passes: FP32 pairs on a "
                          "planar-pair basis (default) or FP64 multiply-adds")
+    ap.add_argument("--chain-arith", default="f32x2", choices=["fp64", "f32x2"],
+                    help="arithmetic of the FP64-accurate Fourier chains (true residuals, right-hand side): "
+                         "FP32 pairs (default) or FP64")
     ap.add_argument("--pass-plan", default="five", choices=["five", "cluster"],
                     help="3D FP32 round trips: five HBM passes, or x/y transforms in one cluster per plane")
     ap.add_argument("--n", type=int, default=128,
@@ -352,7 +371,9 @@ def main():
     ctx = L.Context(n)
     prm = L.Params(alpha=w["alpha"], k=w["k"], theta=0.5, lam=w["lam"], h_ext=w["h"])
     gs = L.GS_F32X2 if args.gs_arith == "f32x2" else L.GS_FP64
-    opts = L.Opts(restart=30, rtol=1e-10, precision=L.PREC_FP32_FLEX, picard_tol=1e-10, picard_max=50, gs_arith=gs)
+    ch = L.CHAIN_F32X2 if args.chain_arith == "f32x2" else L.CHAIN_FP64
+    opts = L.Opts(restart=30, rtol=1e-10, precision=L.PREC_FP32_FLEX, picard_tol=1e-10, picard_max=50, gs_arith=gs,
+                  chain_arith=ch)
     ctx.set_pass_plan(L.PLAN_CLUSTER if args.pass_plan == "cluster" else L.PLAN_FIVE)
     tuning = ctx.autotune()           # launch shapes of the axis passes, picked on this device
     m0 = torch.tensor(I.smooth3d(n), device="cuda")
@@ -447,13 +468,12 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": ("f32+f64 (FP32 FFT-HSS + inner matvec; Gram-Schmidt in FP32-pair arithmetic on a basis whose "
-                  "first vector is FP64 and later ones FP32 pairs; FP64 least squares, true residual, update)"
-                  if gs == L.GS_F32X2 else "f32+f64 (FP32 FFT-HSS + inner matvec, FP64 Arnoldi)"),
+        "dtype": dtype_string(gs, ch),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(n), "nodes": N, "unknowns": 4 * N, "alpha": w["alpha"],
                    "dt": w["k"], "dt_over_explicit_limit": 4.0, "lambda": w["lam"], "h_ext": list(w["h"]),
                    "restart": 30, "rtol": 1e-10, "picard_tol": 1e-10, "gram_schmidt": args.gs_arith,
+                   "fp64_accurate_chains": args.chain_arith,
                    "pass_plan": args.pass_plan,
                    "l2": "inputs larger than L2 (fields 50-67 MB each, Krylov basis ~2 GB)",
                    "parallelism": f"replicas x{world} (independent problems, no collective)"},

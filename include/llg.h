@@ -54,6 +54,8 @@ enum { LLG_PREC_FP64 = 0, LLG_PREC_FP32_FLEX = 1 };
 enum { LLG_PC_FFTHSS = 0, LLG_PC_HERMITIAN = 1, LLG_PC_NONE = 2 };
 /* arithmetic of the Gram--Schmidt passes (llg_opts.gs_arith) */
 enum { LLG_GS_FP64 = 0, LLG_GS_F32X2 = 1 };
+/* arithmetic of the FP64-accurate Fourier chains outside the Krylov cycles (llg_opts.chain_arith) */
+enum { LLG_CHAIN_FP64 = 0, LLG_CHAIN_F32X2 = 1 };
 /* pass plan of 3D FP32 Fourier round trips (llg_set_pass_plan) */
 enum { LLG_PLAN_FIVE = 0, LLG_PLAN_CLUSTER = 1 };
 
@@ -110,6 +112,14 @@ typedef struct {
                            vector, the true residual, the Hessenberg least squares and the
                            solution stay FP64.
                            Used by FP32_FLEX solves with restart <= 32; other solves run FP64. */
+    int chain_arith;    /* arithmetic of the Fourier chains that the method needs to FP64 accuracy
+                           outside the Krylov cycles: the true residual b - A x of every cycle
+                           (Sec. 3.3) and the step's right-hand side (no counterpart in the
+                           paper): LLG_CHAIN_FP64 = FP64; LLG_CHAIN_F32X2 = FP32-pair arithmetic
+                           (sums by two-sum, products by Dekker's exact product; about 47
+                           significant bits, errors a few 2^-48 of the operands' magnitudes),
+                           which runs the FFTs on the FP32 pipes.  FP64 inputs and outputs
+                           either way.  Grids with an axis length outside 64..1024 run FP64. */
 } llg_opts;
 
 typedef struct {
@@ -148,6 +158,12 @@ long long llg_nodes(const llg_ctx *ctx);
    nodal formulas of eqs. (S), (Lambda)).  m: 3 planes; x, y: 4 planes; FP64. */
 llg_status llg_saddle_apply(llg_ctx *ctx, const llg_params *prm, const double *m, const double *x,
                             double *y, int transpose);
+/* The same matvec with its Fourier chain in FP32-pair arithmetic (llg_opts.chain_arith =
+   LLG_CHAIN_F32X2; no counterpart in the paper): FP64 inputs and outputs, same layout, errors a
+   few 2^-48 of the operands' magnitudes per operation instead of 2^-53.  Returns
+   LLG_ERR_UNSUPPORTED_SIZE when an axis length is outside 64..1024. */
+llg_status llg_saddle_apply_f32x2(llg_ctx *ctx, const llg_params *prm, const double *m, const double *x,
+                                  double *y, int transpose);
 
 /* FFT--HSS preconditioner z = M^{-1} p with M = (H + lambda I)(S + lambda I) (Sec. 3.2):
    Algorithm 1 (Fourier solve of the shifted exchange block, multiplier / lambda) followed by

@@ -17,11 +17,11 @@ import ctypes as C
 from dataclasses import dataclass, field
 
 from . import _abi
-from ._abi import EX_FD2, EX_SPECTRAL, GS_F32X2, GS_FP64, PLAN_CLUSTER, PLAN_FIVE, PC_FFTHSS, PC_HERMITIAN, PC_NONE, PREC_FP32_FLEX, PREC_FP64
+from ._abi import CHAIN_F32X2, CHAIN_FP64, EX_FD2, EX_SPECTRAL, GS_F32X2, GS_FP64, PLAN_CLUSTER, PLAN_FIVE, PC_FFTHSS, PC_HERMITIAN, PC_NONE, PREC_FP32_FLEX, PREC_FP64
 
 __all__ = [
     "LLGError", "Params", "Opts", "Context", "EX_SPECTRAL", "EX_FD2", "PREC_FP64", "PREC_FP32_FLEX",
-    "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_precond_saddle_apply",
+    "llg_saddle_apply", "llg_saddle_apply_f32x2", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_precond_saddle_apply",
     "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy", "Ensemble",
 ]
 
@@ -81,12 +81,14 @@ class Opts:
     diagnostics: int = 0
     preconditioner: int = PC_FFTHSS
     gs_arith: int = GS_FP64
+    chain_arith: int = CHAIN_FP64
 
     def c(self):
         o = _abi.Opts()
         o.restart, o.max_iters, o.rtol, o.precision = self.restart, self.max_iters, self.rtol, self.precision
         o.picard_max, o.picard_tol, o.diagnostics = self.picard_max, self.picard_tol, self.diagnostics
         o.preconditioner, o.gs_arith = self.preconditioner, self.gs_arith
+        o.chain_arith = self.chain_arith
         return o
 
 
@@ -201,6 +203,14 @@ def llg_saddle_apply(ctx: Context, prm: Params, m, x, transpose=False, out=None)
     y = out if out is not None else ctx.empty(4)
     ctx._check(ctx.lib.llg_saddle_apply(ctx.h, C.byref(prm.c(ctx)), ctx._arr(m, 3), ctx._arr(x, 4), ctx._arr(y, 4),
                                         int(transpose)))
+    return y
+
+
+def llg_saddle_apply_f32x2(ctx: Context, prm: Params, m, x, transpose=False, out=None):
+    """The saddle matvec with its Fourier chain in FP32-pair arithmetic (FP64 in and out)."""
+    y = out if out is not None else ctx.empty(4)
+    ctx._check(ctx.lib.llg_saddle_apply_f32x2(ctx.h, C.byref(prm.c(ctx)), ctx._arr(m, 3), ctx._arr(x, 4),
+                                              ctx._arr(y, 4), int(transpose)))
     return y
 
 

@@ -27,12 +27,13 @@ EX_SPECTRAL, EX_FD2 = 0, 1
 PREC_FP64, PREC_FP32_FLEX = 0, 1
 PC_FFTHSS, PC_HERMITIAN, PC_NONE = 0, 1, 2
 GS_FP64, GS_F32X2 = 0, 1
+CHAIN_FP64, CHAIN_F32X2 = 0, 1
 PLAN_FIVE, PLAN_CLUSTER = 0, 1
 
 # every symbol the header declares, in declaration order
 EXPORTS = [
     "llg_create", "llg_destroy", "llg_last_error", "llg_set_stream", "llg_launch_count", "llg_nodes",
-    "llg_saddle_apply", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_ffthss_apply_noalloc",
+    "llg_saddle_apply", "llg_saddle_apply_f32x2", "llg_ffthss_apply", "llg_ffthss_apply_f32", "llg_ffthss_apply_noalloc",
     "llg_precond_saddle_apply",
     "llg_gmres_solve", "llg_step_euler", "llg_step_midpoint", "llg_adjoint_step", "llg_energy",
     "llg_lower_order_field",
@@ -57,7 +58,8 @@ class Params(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("restart", C.c_int), ("max_iters", C.c_int), ("rtol", C.c_double), ("precision", C.c_int),
                 ("picard_max", C.c_int), ("picard_tol", C.c_double), ("diagnostics", C.c_int),
-                ("preconditioner", C.c_int), ("gs_arith", C.c_int)]
+                ("preconditioner", C.c_int), ("gs_arith", C.c_int),
+                ("chain_arith", C.c_int)]
 
 
 class Problem(C.Structure):
@@ -98,6 +100,7 @@ def lib():
     L.llg_nodes.argtypes = [ctx]
     L.llg_nodes.restype = C.c_longlong
     L.llg_saddle_apply.argtypes = [ctx, P(Params), vp, vp, vp, C.c_int]
+    L.llg_saddle_apply_f32x2.argtypes = [ctx, P(Params), vp, vp, vp, C.c_int]
     L.llg_ffthss_apply.argtypes = [ctx, P(Params), vp, vp, vp, C.c_int]
     L.llg_ffthss_apply_f32.argtypes = [ctx, P(Params), vp, vp, vp, C.c_int]
     L.llg_ffthss_apply_noalloc.argtypes = [P(Grid), P(Params), vp, vp, vp, C.c_int, vp]

@@ -357,6 +357,8 @@ llg_status check_opts(llg_ctx *c, const llg_opts *o) {
         return set_error(c, LLG_ERR_INVALID_ARG, "unknown preconditioner");
     if (o->gs_arith != LLG_GS_FP64 && o->gs_arith != LLG_GS_F32X2)
         return set_error(c, LLG_ERR_INVALID_ARG, "unknown Gram-Schmidt arithmetic");
+    if (o->chain_arith != LLG_CHAIN_FP64 && o->chain_arith != LLG_CHAIN_F32X2)
+        return set_error(c, LLG_ERR_INVALID_ARG, "unknown Fourier-chain arithmetic");
     return LLG_OK;
 }
 
@@ -398,7 +400,7 @@ llg_status sync_scalars(llg_ctx *c, int count) {
 }
 
 template <typename TIn, typename TOut, typename T>
-NodalIO<TIn, TOut, T> make_io(const T *m, const TIn *x, TOut *y, const double *scale, double lam) {
+NodalIO<TIn, TOut, T> make_io(const nodal_t<T> *m, const TIn *x, TOut *y, const double *scale, double lam) {
     NodalIO<TIn, TOut, T> io;
     std::memset(&io, 0, sizeof(io));
     io.m = m; io.x = x; io.y = y; io.scale = scale; io.lam = (T)lam;
@@ -420,6 +422,14 @@ llg_status op_matvec64(llg_ctx *c, const llg_params *p, double theta, const doub
     io.transpose = transpose;
     io.skip = skip;
     return spectral_chain<double, double, double>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
+}
+
+// the same matvec (unscaled, untransposed) with the Fourier chain in FP32-pair arithmetic
+llg_status op_matvec_pair(llg_ctx *c, const llg_params *p, double theta, const double *m, const double *x, double *y,
+                          int transpose = 0) {
+    auto io = make_io<double, double, fpair>(m, x, y, nullptr, p->lambda);
+    io.transpose = transpose;
+    return spectral_chain<fpair, double, double>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
 }
 
 llg_status op_apply64(llg_ctx *c, const llg_params *p, double theta, const double *m, const double *x,
@@ -474,7 +484,11 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
     const bool flex = o->precision == LLG_PREC_FP32_FLEX;
     if ((st = ensure_spec(c, true, flex)) != LLG_OK) return st;
     SolveOps ops;
-    ops.matvec = [=](const double *xx, double *yy) { return op_matvec64(c, p, theta, m, xx, nullptr, yy, 0); };
+    // the true residuals: FP64 chain, or the FP32-pair chain where every axis has one
+    if (o->chain_arith == LLG_CHAIN_F32X2 && pair_chains_available(c))
+        ops.matvec = [=](const double *xx, double *yy) { return op_matvec_pair(c, p, theta, m, xx, yy); };
+    else
+        ops.matvec = [=](const double *xx, double *yy) { return op_matvec64(c, p, theta, m, xx, nullptr, yy, 0); };
     const int pc = o->preconditioner;
     // operators issued inside a GMRES cycle return at once once the cycle's stopping flag
     // is set (the host may have queued one more step); v_0 and the true residual,
@@ -549,17 +563,23 @@ llg_status lowfield_nodal(llg_ctx *c, const llg_params *p, const double *m, doub
     return cuda_check(c, cudaGetLastError(), "lower-order field");
 }
 
-llg_status rhs_velocity(llg_ctx *c, const llg_params *p, const double *m, const double *hf, double *b) {
+template <typename T>
+llg_status rhs_velocity_t(llg_ctx *c, const llg_params *p, const double *m, const double *hf, double *b) {
     // f = Chat Lap_N m + (1 + alpha^2) (h_ext + per-node part of h_low) ; multiplier row 0
-    auto io = make_io<double, double, double>(m, m, b, nullptr, p->lambda);
+    auto io = make_io<double, double, T>(m, m, b, nullptr, p->lambda);
     const double s = 1.0 + p->alpha * p->alpha;
-    io.fld[0] = s * p->h_ext[0];
-    io.fld[1] = s * p->h_ext[1];
-    io.fld[2] = s * p->h_ext[2];
+    for (int q = 0; q < 3; ++q) io.fld[q] = (T)(s * p->h_ext[q]);
     io.hf = hf;
     io.hs = s;
     Symbol sym{0.0, -chat(p), 1.0 / (double)c->geo.N, 0, p->exchange};
-    return spectral_chain<double, double, double>(c, IN_M, OUT_FIELD, io, sym);
+    return spectral_chain<T, double, double>(c, IN_M, OUT_FIELD, io, sym);
+}
+
+// the right-hand side in the arithmetic opts->chain_arith asks for (FP64 where the grid has
+// no FP32-pair chain)
+llg_status rhs_velocity(llg_ctx *c, const llg_params *p, const llg_opts *o, const double *m, const double *hf, double *b) {
+    if (o->chain_arith == LLG_CHAIN_F32X2 && pair_chains_available(c)) return rhs_velocity_t<fpair>(c, p, m, hf, b);
+    return rhs_velocity_t<double>(c, p, m, hf, b);
 }
 
 llg_status energy_async(llg_ctx *c, const llg_params *p, const double *m, double *tmp, double *dst_dev) {
@@ -646,6 +666,25 @@ llg_status llg_create(const llg_grid *grid, void *cuda_stream, llg_ctx **out) {
             s64[0][i] = sp; s64[1][i] = fd;
             s32[0][i] = (float)sp; s32[1][i] = (float)fd;
         }
+        // FP32 pairs: hi = the value rounded to FP32, lo = the rest rounded to FP32
+        std::vector<cfpair> tp(n);
+        std::vector<fpair> sp2[2];
+        for (int i = 0; i < n; ++i) {
+            const long double ang = twopi * (long double)i / (long double)n;
+            const long double cr = cosl(ang), ci = -sinl(ang);
+            tp[i].x = fpair((float)cr, (float)(cr - (long double)(float)cr));
+            tp[i].y = fpair((float)ci, (float)(ci - (long double)(float)ci));
+        }
+        for (int ex = 0; ex < 2; ++ex) {
+            sp2[ex].resize(n);
+            for (int i = 0; i < n; ++i) sp2[ex][i] = fpair(s64[ex][i]);
+        }
+        if ((e = cudaMalloc(&c->twp[l], sizeof(cfpair) * n)) != cudaSuccess) return fail(e, "tables");
+        cudaMemcpy(c->twp[l], tp.data(), sizeof(cfpair) * n, cudaMemcpyHostToDevice);
+        for (int ex = 0; ex < 2; ++ex) {
+            if ((e = cudaMalloc(&c->sigp[ex][l], sizeof(fpair) * n)) != cudaSuccess) return fail(e, "tables");
+            cudaMemcpy(c->sigp[ex][l], sp2[ex].data(), sizeof(fpair) * n, cudaMemcpyHostToDevice);
+        }
         if ((e = cudaMalloc(&c->tw64[l], sizeof(double2) * n)) != cudaSuccess) return fail(e, "tables");
         if ((e = cudaMalloc(&c->tw32[l], sizeof(float2) * n)) != cudaSuccess) return fail(e, "tables");
         cudaMemcpy(c->tw64[l], t64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
@@ -695,7 +734,8 @@ llg_status llg_destroy(llg_ctx *c) {
     for (int l = 0; l < 3; ++l) {
         cudaFree(c->tw64[l]);
         cudaFree(c->tw32[l]);
-        for (int ex = 0; ex < 2; ++ex) { cudaFree(c->sig64[ex][l]); cudaFree(c->sig32[ex][l]); }
+        cudaFree(c->twp[l]);
+        for (int ex = 0; ex < 2; ++ex) { cudaFree(c->sig64[ex][l]); cudaFree(c->sig32[ex][l]); cudaFree(c->sigp[ex][l]); }
     }
     cudaFree(c->spec64); cudaFree(c->spec32); cudaFree(c->red); cudaFree(c->dsc);
     cudaFree(c->gdev); cudaFree(c->m32); cudaFree(c->aux); cudaFree(c->dem_tab);
@@ -850,6 +890,17 @@ llg_status llg_saddle_apply(llg_ctx *c, const llg_params *p, const double *m, co
     return op_matvec64(c, p, p->theta, m, x, nullptr, y, transpose);
 }
 
+llg_status llg_saddle_apply_f32x2(llg_ctx *c, const llg_params *p, const double *m, const double *x, double *y,
+                                  int transpose) {
+    LLG_GUARD(c);
+    llg_status st = check_params(c, p);
+    if (st != LLG_OK) return st;
+    if (!m || !x || !y) return set_error(c, LLG_ERR_INVALID_ARG, "null array");
+    if ((st = ensure_spec(c, true, false)) != LLG_OK) return st;
+    if (!pair_chains_available(c)) return set_error(c, LLG_ERR_UNSUPPORTED_SIZE, "FP32-pair chain: axis length outside 64..1024");
+    return op_matvec_pair(c, p, p->theta, m, x, y, transpose);
+}
+
 llg_status llg_ffthss_apply(llg_ctx *c, const llg_params *p, const double *m, const double *pin, double *z, int transpose) {
     LLG_GUARD(c);
     llg_status st = check_params(c, p);
@@ -948,7 +999,7 @@ llg_status llg_step_euler(llg_ctx *c, const llg_params *p, const llg_opts *o, co
     }
     const double *hf = nullptr;
     if ((st = lowfield_nodal(c, p, m_n, c->aux + 18 * N, &hf)) != LLG_OK) return st;
-    if ((st = rhs_velocity(c, p, m_n, hf, b)) != LLG_OK) return st;
+    if ((st = rhs_velocity(c, p, o, m_n, hf, b)) != LLG_OK) return st;
     cudaMemsetAsync(x_out, 0, sizeof(double) * 4 * N, c->stream);
     st = solve(c, p, 1.0, o, m_n, b, x_out, &inf);
     if (st != LLG_OK && st != LLG_ERR_NOT_CONVERGED) { inf.status = st; if (info) *info = inf; return st; }
@@ -999,7 +1050,7 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
     const double *hf = nullptr;
     k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, v_prev, 0.5 * p->k, mhat, 3 * N);
     if ((st = lowfield_nodal(c, p, mhat, hfbuf, &hf)) != LLG_OK) return st;
-    if ((st = rhs_velocity(c, p, m_n, hf, b)) != LLG_OK) return st;
+    if ((st = rhs_velocity(c, p, o, m_n, hf, b)) != LLG_OK) return st;
     // warm start (v_prev | 0), or zero
     if (v_prev) cudaMemcpyAsync(x_out, v_prev, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
     else cudaMemsetAsync(x_out, 0, sizeof(double) * 3 * N, c->stream);
@@ -1031,7 +1082,7 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
             k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, 3 * N);
             c->launches++;
             if ((st = lowfield_nodal(c, p, mhat, hfbuf, &hf)) != LLG_OK) return st;
-            if ((st = rhs_velocity(c, p, m_n, hf, b)) != LLG_OK) return st;
+            if ((st = rhs_velocity(c, p, o, m_n, hf, b)) != LLG_OK) return st;
             have_r0 = false;
             continue;
         }

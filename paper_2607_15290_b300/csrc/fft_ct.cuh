@@ -58,7 +58,7 @@ struct ColL {
 
 template <int SIGN, typename C>
 __device__ __forceinline__ C tw_load(const C *__restrict__ tw, int i) {
-    C w = __ldg(&tw[i]);
+    C w = ldg_ro(&tw[i]);
     if (SIGN > 0) w.y = -w.y;
     return w;
 }

@@ -12,6 +12,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include "fpair.cuh"
 
 namespace llg {
 
@@ -27,6 +28,8 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
+// SIGN * v for SIGN = +-1 (a negation, for every scalar type)
+template <int SIGN, typename T> __device__ __forceinline__ T sgn(T v) { return SIGN > 0 ? v : -v; }
 // multiply by SIGN * i
 template <int SIGN, typename C> __device__ __forceinline__ C cmul_i(C a) {
     return SIGN > 0 ? cmk<C>(-a.y, a.x) : cmk<C>(a.y, -a.x);
@@ -53,9 +56,9 @@ template <int SIGN, typename C> __device__ __forceinline__ void dft8(C (&a)[8]) 
     dft4<SIGN>(e0, e1, e2, e3);
     dft4<SIGN>(o0, o1, o2, o3);
     // o_k *= W8^k, W8 = exp(SIGN 2 pi i / 8)
-    C w1 = cmk<C>((o1.x - SIGN * o1.y) * h, (o1.y + SIGN * o1.x) * h);
+    C w1 = cmk<C>((o1.x - sgn<SIGN>(o1.y)) * h, (o1.y + sgn<SIGN>(o1.x)) * h);
     C w2 = cmul_i<SIGN>(o2);
-    C w3 = cmk<C>((-o3.x - SIGN * o3.y) * h, (-o3.y + SIGN * o3.x) * h);
+    C w3 = cmk<C>((-o3.x - sgn<SIGN>(o3.y)) * h, (-o3.y + sgn<SIGN>(o3.x)) * h);
     a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
     a[1] = cadd(e1, w1); a[5] = csub(e1, w1);
     a[2] = cadd(e2, w2); a[6] = csub(e2, w2);

@@ -7,6 +7,7 @@
 #include <functional>
 #include <vector>
 #include "../../include/llg.h"
+#include "fpair.cuh"
 
 namespace llg {
 
@@ -71,9 +72,14 @@ struct Symbol {
     int exchange;   // which sigma table
 };
 
+// storage of the nodal fields a chain of compute type T reads (FP32-pair chains read FP64)
+template <typename T> struct nodal_store { using type = T; };
+template <> struct nodal_store<fpair> { using type = double; };
+template <typename T> using nodal_t = typename nodal_store<T>::type;
+
 template <typename TIn, typename TOut, typename T>
 struct NodalIO {
-    const T *m;            // nodal field used by the prologue/epilogue (3 planes, precision T)
+    const nodal_t<T> *m;   // nodal field used by the prologue/epilogue (3 planes)
     const TIn *x;          // input planes (4 planes; 3 for IN_M)
     TOut *y;               // output planes (4)
     const double *scale;   // optional device scalar s (NULL = 1)
@@ -81,8 +87,8 @@ struct NodalIO {
     T fld[3];
     int transpose;         // OUT_MATVEC: use A^T
     // OUT_JT only
-    const T *mn;           // m^n (3 planes)
-    const T *vf;           // forward velocity v (3 planes) and r (1 plane, at vf + 3N)
+    const nodal_t<T> *mn;  // m^n (3 planes)
+    const nodal_t<T> *vf;  // forward velocity v (3 planes) and r (1 plane, at vf + 3N)
     T half_k;              // k / 2
     // OUT_APPLY / OUT_FUSED: 1 = skip the nodal 4x4 inverse (the shifted symmetric-part
     // preconditioner (lambda I + H)^{-1} alone)
@@ -138,6 +144,9 @@ struct llg_ctx {
     // per-axis symbol tables sigma_axis(index) for [spectral, fd2]
     double *sig64[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     float *sig32[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    // the same twiddle and symbol tables as FP32 pairs (FP64-accurate chains on the FP32 pipes)
+    llg::cfpair *twp[3] = {nullptr, nullptr, nullptr};
+    llg::fpair *sigp[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     double2 *spec64 = nullptr;   // spectral scratch, rows * S
     float2 *spec32 = nullptr;
     double *red = nullptr;       // reduction partials
@@ -186,6 +195,8 @@ void prof_discard(llg_ctx *c, size_t first, int min_tag);
 llg_status autotune(llg_ctx *c, int prec_mask, std::string *report);
 // FP64 Fourier transform along axis 1 (3D y) of every spectral column, no multiplier
 llg_status plain_axis_pass64(llg_ctx *c, int axis, bool forward);
+// every axis of the grid has a compile-time-length pass (the FP32-pair chains need one)
+bool pair_chains_available(const llg_ctx *c);
 
 // demag.cu: h = periodic zero-mean demagnetising field of m (3 planes, FP64; uses the FP64
 // spectral buffer); h += 2 k_an (e . m) e

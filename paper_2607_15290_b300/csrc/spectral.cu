@@ -31,12 +31,22 @@ namespace llg {
 template <typename T> static const cplx<T> *tw_of(llg_ctx *c, int axis);
 template <> const double2 *tw_of<double>(llg_ctx *c, int axis) { return c->tw64[axis]; }
 template <> const float2 *tw_of<float>(llg_ctx *c, int axis) { return c->tw32[axis]; }
+template <> const cfpair *tw_of<fpair>(llg_ctx *c, int axis) { return c->twp[axis]; }
 template <typename T> static const T *sig_of(llg_ctx *c, int ex, int axis);
 template <> const double *sig_of<double>(llg_ctx *c, int ex, int axis) { return c->sig64[ex][axis]; }
 template <> const float *sig_of<float>(llg_ctx *c, int ex, int axis) { return c->sig32[ex][axis]; }
+template <> const fpair *sig_of<fpair>(llg_ctx *c, int ex, int axis) { return c->sigp[ex][axis]; }
 template <typename T> static cplx<T> *spec_of(llg_ctx *c);
 template <> double2 *spec_of<double>(llg_ctx *c) { return c->spec64; }
 template <> float2 *spec_of<float>(llg_ctx *c) { return c->spec32; }
+// FP32-pair chains use the FP64 buffer (a complex pair is 16 bytes, as a complex double)
+template <> cfpair *spec_of<fpair>(llg_ctx *c) { return reinterpret_cast<cfpair *>(c->spec64); }
+
+bool pair_chains_available(const llg_ctx *c) {
+    const SpecGeom &g = c->geo;
+    return c->twp[0] != nullptr && c->spec64 != nullptr && ct::covers(g.logn[0]) && ct::covers(g.logn[1]) &&
+           (g.dim == 2 || ct::covers(g.logn[2]));
+}
 
 template <typename T, typename TIn, typename TOut, int E>
 static cudaError_t launch_row_fwd_E(llg_ctx *c, int in_mode, RowArgs<T, TIn, TOut> a, int blocks, int threads, size_t sm) {
@@ -184,7 +194,9 @@ static cudaError_t launch_col_cfg(llg_ctx *c, int mode, const ColArgs<T> &a, int
     }
     if (ct::covers(a.logn) && cfg.E == col_E<T>(a.nl)) return ct::col<T>(c, a.logn, mode, a, grid, cfg.TW);
 #define LLG_CE(EE, TT) if (cfg.E == EE && cfg.TW == TT) return launch_col_ETW<T, EE, TT>(c, mode, a, grid);
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (is_fpair<T>::value) {
+        return cudaErrorInvalidValue;   // compile-time lengths only
+    } else if constexpr (sizeof(T) == 8) {
         LLG_CE(2, 8) LLG_CE(4, 8) LLG_CE(8, 8) LLG_CE(2, 4) LLG_CE(4, 4) LLG_CE(8, 4)
     } else {
         LLG_CE(2, 16) LLG_CE(4, 16) LLG_CE(8, 16) LLG_CE(16, 16) LLG_CE(2, 8) LLG_CE(4, 8) LLG_CE(8, 8) LLG_CE(16, 8)
@@ -303,8 +315,12 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
             else e = cudaErrorInvalidValue;                                                   \
             break;                                                                            \
     }
+    if constexpr (is_fpair<T>::value) {
+        if (!pair_chains_available(c)) return set_error(c, LLG_ERR_UNSUPPORTED_SIZE, "FP32-pair chain: axis length outside 64..1024");
+    }
     prof_begin(c, K_XFWD, in_b + live * CB, xf);
     if (rct) e = ct::row_fwd<T, TIn, TOut>(c, g.logn[0], in_mode, ra, blocks, threads, smr);
+    else if constexpr (is_fpair<T>::value) e = cudaErrorInvalidValue;
     else { LLG_DISPATCH_E(launch_row_fwd_E, in_mode) }
     prof_end(c);
     if (e != cudaSuccess) return cuda_check(c, e, "x-pass forward");
@@ -333,6 +349,7 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
     }
     prof_begin(c, K_XINV, live * CB + out_b, xf);
     if (rct) e = ct::row_inv<T, TIn, TOut>(c, g.logn[0], out_mode, ra, blocks, threads, smr);
+    else if constexpr (is_fpair<T>::value) e = cudaErrorInvalidValue;
     else { LLG_DISPATCH_E(launch_row_inv_E, out_mode) }
     prof_end(c);
 #undef LLG_DISPATCH_E
@@ -489,5 +506,6 @@ template llg_status spectral_chain<double, double, double>(llg_ctx *, int, int, 
 template llg_status spectral_chain<float, double, float>(llg_ctx *, int, int, const NodalIO<double, float, float> &, const Symbol &);
 template llg_status spectral_chain<float, float, double>(llg_ctx *, int, int, const NodalIO<float, double, float> &, const Symbol &);
 template llg_status spectral_chain<float, float, float>(llg_ctx *, int, int, const NodalIO<float, float, float> &, const Symbol &);
+template llg_status spectral_chain<fpair, double, double>(llg_ctx *, int, int, const NodalIO<double, double, fpair> &, const Symbol &);
 
 }  // namespace llg

@@ -68,7 +68,7 @@ __device__ __forceinline__ void row_fwd_ct_body_to(const RowArgs<T, TIn, TOut> &
                 for (int q = 0; q < NX; ++q) xv[k][q] = io.x[q * Nn + j];
                 if constexpr (NEED_M) {
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) mv[k][q] = io.m[q * Nn + j];
+                    for (int q = 0; q < 3; ++q) mv[k][q] = cvt<T>(io.m[q * Nn + j]);
                 }
             }
         }
@@ -235,15 +235,15 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
             const long long j = j0 + idx;
             if (idx < total && j < Nn) {
                 if constexpr (NEED_M) {
-                    const T *mp = OUT == OUT_JT ? io.mn : io.m;
+                    const nodal_t<T> *mp = OUT == OUT_JT ? io.mn : io.m;
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) mv[k][q] = mp[q * Nn + j];
+                    for (int q = 0; q < 3; ++q) mv[k][q] = cvt<T>(mp[q * Nn + j]);
                 }
 #pragma unroll
                 for (int q = XLO; q < XHI; ++q) xv[k][q] = io.x[q * Nn + j];
                 if constexpr (NEED_F) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) fv[k][q] = io.vf[q * Nn + j];
+                    for (int q = 0; q < 4; ++q) fv[k][q] = cvt<T>(io.vf[q * Nn + j]);
                 }
             }
         }
@@ -273,17 +273,20 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
                 const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];
                 const T v1 = s * cvt<T>(xv[k][0]), v2 = s * cvt<T>(xv[k][1]), v3 = s * cvt<T>(xv[k][2]);
                 const T r = s * cvt<T>(xv[k][3]);
-                const T sg = io.transpose ? (T)-1 : (T)1;
-                y[j] = cvt<TOut>(w1 + sg * (m2 * v3 - m3 * v2 + m1 * r));
-                y[Nn + j] = cvt<TOut>(w2 + sg * (m3 * v1 - m1 * v3 + m2 * r));
-                y[2 * Nn + j] = cvt<TOut>(w3 + sg * (m1 * v2 - m2 * v1 + m3 * r));
-                y[3 * Nn + j] = cvt<TOut>(-sg * (m1 * v1 + m2 * v2 + m3 * v3));
+                // the transpose flips the signs of the skew part (exact negations)
+                const bool tr = io.transpose != 0;
+                const T k1 = m2 * v3 - m3 * v2 + m1 * r, k2 = m3 * v1 - m1 * v3 + m2 * r;
+                const T k3 = m1 * v2 - m2 * v1 + m3 * r, k4 = m1 * v1 + m2 * v2 + m3 * v3;
+                y[j] = cvt<TOut>(w1 + (tr ? -k1 : k1));
+                y[Nn + j] = cvt<TOut>(w2 + (tr ? -k2 : k2));
+                y[2 * Nn + j] = cvt<TOut>(w3 + (tr ? -k3 : k3));
+                y[3 * Nn + j] = cvt<TOut>(tr ? k4 : -k4);
             } else if constexpr (OUT == OUT_FIELD) {
                 T f1 = w1 + io.fld[0], f2 = w2 + io.fld[1], f3 = w3 + io.fld[2];
                 if (io.hf) {
-                    f1 += (T)(io.hs * io.hf[j]);
-                    f2 += (T)(io.hs * io.hf[Nn + j]);
-                    f3 += (T)(io.hs * io.hf[2 * Nn + j]);
+                    f1 += cvt<T>(io.hs * io.hf[j]);
+                    f2 += cvt<T>(io.hs * io.hf[Nn + j]);
+                    f3 += cvt<T>(io.hs * io.hf[2 * Nn + j]);
                 }
                 y[j] = cvt<TOut>(f1);
                 y[Nn + j] = cvt<TOut>(f2);
@@ -323,6 +326,7 @@ __global__ void __launch_bounds__(512) row_inv_ct(RowArgs<T, TIn, TOut> a) {
 template <typename T> __device__ __forceinline__ T symbol_div(T num, T den);
 template <> __device__ __forceinline__ float symbol_div<float>(float num, float den) { return __fdividef(num, den); }
 template <> __device__ __forceinline__ double symbol_div<double>(double num, double den) { return num / den; }
+template <> __device__ __forceinline__ fpair symbol_div<fpair>(fpair num, fpair den) { return num / den; }
 
 template <typename T, int LOGN, int E, class L, typename C>
 __device__ __forceinline__ void apply_symbol(C (&v)[E], const ColArgs<T> &a, int col, int by, int t) {
@@ -334,7 +338,7 @@ __device__ __forceinline__ void apply_symbol(C (&v)[E], const ColArgs<T> &a, int
     const T base = sx + sb;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
-        const T d = a.sa + a.sb * (base + __ldg(&a.tl[t + P * q]));
+        const T d = a.sa + a.sb * (base + ldg_ro(&a.tl[t + P * q]));
         const T mult = live ? (a.sinv ? symbol_div<T>(a.sscale, d) : a.sscale * d) : (T)0;
         v[q] = cscale(v[q], mult);
     }

@@ -32,8 +32,15 @@ cudaError_t row_fwd_launch(llg_ctx *c, int in_mode, const RowArgs<T, TIn, TOut> 
         if (e != cudaSuccess) return e;                                \
         return launch_pdl(k, dim3(blocks), dim3(threads), sm, c->stream, a); \
     }
-    switch (in_mode) {
-        LLG_RF(IN_V) LLG_RF(IN_FUSED) LLG_RF(IN_M) LLG_RF(IN_NODAL_T)
+    if constexpr (is_fpair<T>::value) {
+        // FP32-pair chains: the true residual and the right-hand side only
+        switch (in_mode) {
+            LLG_RF(IN_V) LLG_RF(IN_M)
+        }
+    } else {
+        switch (in_mode) {
+            LLG_RF(IN_V) LLG_RF(IN_FUSED) LLG_RF(IN_M) LLG_RF(IN_NODAL_T)
+        }
     }
 #undef LLG_RF
     return cudaErrorInvalidValue;
@@ -48,8 +55,14 @@ cudaError_t row_inv_launch(llg_ctx *c, int out_mode, const RowArgs<T, TIn, TOut>
         if (e != cudaSuccess) return e;                                \
         return launch_pdl(k, dim3(blocks), dim3(threads), sm, c->stream, a); \
     }
-    switch (out_mode) {
-        LLG_RI(OUT_APPLY) LLG_RI(OUT_FUSED) LLG_RI(OUT_MATVEC) LLG_RI(OUT_FIELD) LLG_RI(OUT_PLAIN) LLG_RI(OUT_JT)
+    if constexpr (is_fpair<T>::value) {
+        switch (out_mode) {
+            LLG_RI(OUT_MATVEC) LLG_RI(OUT_FIELD)
+        }
+    } else {
+        switch (out_mode) {
+            LLG_RI(OUT_APPLY) LLG_RI(OUT_FUSED) LLG_RI(OUT_MATVEC) LLG_RI(OUT_FIELD) LLG_RI(OUT_PLAIN) LLG_RI(OUT_JT)
+        }
     }
 #undef LLG_RI
     return cudaErrorInvalidValue;
@@ -164,8 +177,10 @@ LLG_CT_ROWS(double, double, double)
 LLG_CT_ROWS(float, double, float)
 LLG_CT_ROWS(float, float, double)
 LLG_CT_ROWS(float, float, float)
+LLG_CT_ROWS(fpair, double, double)
 #undef LLG_CT_ROWS
 template cudaError_t col_launch<double, LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<double> &, dim3, int);
+template cudaError_t col_launch<fpair, LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<fpair> &, dim3, int);
 template cudaError_t col_launch<float, LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<float> &, dim3, int);
 template cudaError_t staged_launch<LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<float> &, int, int, int, int);
 template cudaError_t col_v2_launch<LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<float> &, dim3, int);

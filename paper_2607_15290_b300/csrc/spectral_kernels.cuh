@@ -34,7 +34,7 @@ struct ColArgs {
 
 template <typename TIn, typename TOut, typename T>
 __device__ __forceinline__ T in_scale(const NodalIO<TIn, TOut, T> &io) {
-    return io.scale ? (T)(*io.scale) : (T)1;
+    return io.scale ? cvt<T>(*io.scale) : (T)1;
 }
 
 // ------------------------------------------------------------------ x-pass forward
