@@ -311,7 +311,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison and apply sweep legs")
     ap.add_argument("--apply-sweep", default="", help="only time the isolated FFT-HSS apply on these grids, "
                     "e.g. '256^3,128^3,1024^2' (one JSON line each, with a per-pass breakdown)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --apply-sweep")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "matvec-fp64", "matvec-f32x2"],
+                    help="what --apply-sweep times: the FFT-HSS apply (FP32 or FP64), or the saddle matvec with "
+                         "an FP64 or an FP32-pair Fourier chain")
     ap.add_argument("--no-autotune", action="store_true",
                     help="--apply-sweep with the default launch shapes (for profiling the passes alone)")
     ap.add_argument("--ensemble", action="store_true", help="only the 96-problem batched ensemble (5 Euler steps)")
@@ -330,6 +332,9 @@ def main():
     ap.add_argument("--chain-arith", default="f32x2", choices=["fp64", "f32x2"],
                     help="arithmetic of the FP64-accurate Fourier chains (true residuals, right-hand side): "
                          "FP32 pairs (default) or FP64")
+    ap.add_argument("--axis-shapes", default="",
+                    help="skip the autotuner and set the FP32 axis-pass shapes, e.g. "
+                         "'y-forward=register(E8,TW16);z=tma(TW8);y-inverse=register(E8,TW16)'")
     ap.add_argument("--pass-plan", default="five", choices=["five", "cluster"],
                     help="3D FP32 round trips: five HBM passes, or x/y transforms in one cluster per plane")
     ap.add_argument("--n", type=int, default=128,
@@ -375,7 +380,14 @@ def main():
     opts = L.Opts(restart=30, rtol=1e-10, precision=L.PREC_FP32_FLEX, picard_tol=1e-10, picard_max=50, gs_arith=gs,
                   chain_arith=ch)
     ctx.set_pass_plan(L.PLAN_CLUSTER if args.pass_plan == "cluster" else L.PLAN_FIVE)
-    tuning = ctx.autotune()           # launch shapes of the axis passes, picked on this device
+    if args.axis_shapes:
+        # shapes a live run picked, replayed (a profiler distorts the tuner's timings)
+        for item in args.axis_shapes.split(";"):
+            slot, shape = item.split("=")
+            ctx.set_axis_shape(slot.strip(), shape.strip())
+        tuning = "fixed FP32 shapes: " + args.axis_shapes
+    else:
+        tuning = ctx.autotune()       # launch shapes of the axis passes, picked on this device
     m0 = torch.tensor(I.smooth3d(n), device="cuda")
     x = ctx.empty(4)
     mA, mB = m0.clone(), ctx.empty(3)
@@ -660,15 +672,17 @@ def apply_sweep(args):
         N = int(np.prod(n))
         ctx = L.Context(n)
         ctx.set_pass_plan(L.PLAN_CLUSTER if args.pass_plan == "cluster" else L.PLAN_FIVE)
-        tuning = "" if args.no_autotune else ctx.autotune(fp64=args.precision == "fp64", fp32=args.precision == "fp32")
         f32 = args.precision == "fp32"
+        tuning = "" if args.no_autotune else ctx.autotune(fp64=not f32, fp32=f32)
         dt = torch.float32 if f32 else torch.float64
         m = torch.tensor(I.smooth3d(n) if len(n) == 3 else I.smooth2d(n), device="cuda").to(dt)
         p = torch.randn((4,) + tuple(reversed(n)), device="cuda", dtype=dt)
         z = torch.empty_like(p)
         prm = L.Params(alpha=0.1, k=workload_params(max(n))["k"], theta=0.5, lam=0.5)
-        fn = (lambda: L.llg_ffthss_apply_f32(ctx, prm, m, p, out=z)) if f32 else \
-             (lambda: L.llg_ffthss_apply(ctx, prm, m, p, out=z))
+        fn = {"fp32": lambda: L.llg_ffthss_apply_f32(ctx, prm, m, p, out=z),
+              "fp64": lambda: L.llg_ffthss_apply(ctx, prm, m, p, out=z),
+              "matvec-fp64": lambda: L.llg_saddle_apply(ctx, prm, m, p, out=z),
+              "matvec-f32x2": lambda: L.llg_saddle_apply_f32x2(ctx, prm, m, p, out=z)}[args.precision]
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
@@ -682,7 +696,11 @@ def apply_sweep(args):
         w = 4 if f32 else 8
         # the cluster plan's grids (128^2 and 256^2 planes) make three passes of the FP32 apply
         passes = 3 if len(n) == 2 or (args.pass_plan == "cluster" and f32 and n[0] == n[1] and n[0] in (128, 256)) else 5
-        algo = (11 + 6 * (passes - 1)) * w * N
+        # nodal words: the apply reads v (3), then m and r (3 + 1) and writes z (4); the matvec
+        # reads v (3), then m and x (3 + 4) and writes y (4); every spectral pass reads and
+        # writes 3 words a node
+        nodal = 14 if args.precision.startswith("matvec") else 11
+        algo = (nodal + 6 * (passes - 1)) * w * N
         out = {"grid": list(n), "precision": args.precision, "ms_per_apply": ms, "applies_per_s": 1e3 / ms,
                "gbs_algorithmic": algo / ms / 1e6, "frac_of_hbm": algo / ms / 1e6 / pk["hbm_gbs"],
                "algorithmic_bytes": algo, "passes": passes, "autotune": tuning.strip().splitlines()}

@@ -314,6 +314,15 @@ llg_status llg_set_pass_plan(llg_ctx *ctx, int plan);
    synchronises the stream.  Without this call the default shapes are used. */
 llg_status llg_autotune(llg_ctx *ctx, int precision_mask, char *report, int report_len);
 
+/* Set one axis pass's launch shape by hand, as llg_autotune would (no counterpart in the
+   paper; lets a profiler run replay the shapes a live run picked).  fp32: 1 = FP32 passes,
+   0 = FP64; slot: 0 = y pass of 2D grids, 1 = y forward, 2 = z (with the multiplier),
+   3 = y inverse (3D); kind: 0 = register kernel (E points per thread, TW columns), 1 = staged
+   tile (TW columns, CB per sub-batch), 3 = two columns per thread (TW), 4 = TMA-fed persistent
+   kernel (TW).  LLG_ERR_INVALID_ARG when the grid has no such pass or the shape is not one the
+   tuner would try for its line length.  Other passes keep their shapes (defaults if none). */
+llg_status llg_set_axis_shape(llg_ctx *ctx, int fp32, int slot, int kind, int E, int TW, int CB);
+
 /* ---------------------------------------------------------------- measurement support
    (infrastructure for the benchmark; no counterpart in the paper) */
 

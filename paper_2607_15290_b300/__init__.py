@@ -136,6 +136,21 @@ class Context:
         self._check(self.lib.llg_autotune(self.h, mask, buf, len(buf)))
         return buf.value.decode()
 
+    _SLOTS = {"y(2D)": 0, "y-forward": 1, "z": 2, "y-inverse": 3}
+
+    def set_axis_shape(self, slot, shape, fp32=True):
+        """Set one axis pass's launch shape by the tuner's name for it, e.g.
+        set_axis_shape("z", "tma(TW8)") or set_axis_shape("y-forward", "register(E8,TW16)")."""
+        import re
+        m = re.fullmatch(r"(register|staged|paired|tma)\((.*)\)", shape.strip())
+        if not m:
+            raise ValueError(f"unknown axis shape {shape!r}")
+        kv = dict(re.findall(r"([A-Z]+)(\d+)", m.group(2)))
+        kind = {"register": 0, "staged": 1, "paired": 3, "tma": 4}[m.group(1)]
+        E = int(kv.get("E", 8))
+        TW, CB = int(kv.get("TW", 0)), int(kv.get("CB", 0))
+        self._check(self.lib.llg_set_axis_shape(self.h, int(fp32), self._SLOTS[slot], kind, E, TW, CB))
+
     def profile_begin(self, kernel_class):
         """Time every launch of one kernel class ('xfwd', 'axis', 'xinv', 'arnoldi') live."""
         self._check(self.lib.llg_profile_begin(self.h, _abi.KCLASS[kernel_class]))

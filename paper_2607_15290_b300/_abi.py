@@ -39,7 +39,7 @@ EXPORTS = [
     "llg_lower_order_field",
     "llg_ensemble_create", "llg_ensemble_run", "llg_ensemble_set_blocks", "llg_ensemble_max_blocks",
     "llg_ensemble_autotune", "llg_ensemble_set_barrier_test", "llg_ensemble_destroy", "llg_ensemble_last_error",
-    "llg_set_pass_plan", "llg_autotune", "llg_profile_begin", "llg_profile_end", "llg_krylov_orthogonality", "llg_probe_fma_rate",
+    "llg_set_pass_plan", "llg_autotune", "llg_set_axis_shape", "llg_profile_begin", "llg_profile_end", "llg_krylov_orthogonality", "llg_probe_fma_rate",
     "llg_check_conversions",
 ]
 KCLASS = {"xfwd": 1, "axis": 2, "xinv": 3, "arnoldi": 4}
@@ -112,6 +112,7 @@ def lib():
     L.llg_energy.argtypes = [ctx, P(Params), vp, d]
     L.llg_lower_order_field.argtypes = [ctx, P(Params), vp, vp]
     L.llg_autotune.argtypes = [ctx, C.c_int, C.c_char_p, C.c_int]
+    L.llg_set_axis_shape.argtypes = [ctx, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
     L.llg_set_pass_plan.argtypes = [ctx, C.c_int]
     L.llg_ensemble_create.argtypes = [P(Problem), C.c_int, P(Opts), vp, P(vp)]
     L.llg_ensemble_run.argtypes = [vp, C.c_int, P(Info), P(C.c_int)]

@@ -766,6 +766,11 @@ llg_status llg_autotune(llg_ctx *c, int precision_mask, char *report, int report
     return st;
 }
 
+llg_status llg_set_axis_shape(llg_ctx *c, int fp32, int slot, int kind, int E, int TW, int CB) {
+    LLG_GUARD(c);
+    return llg::set_axis_shape(c, fp32, slot, ColCfg{kind, E, TW, CB});
+}
+
 llg_status llg_profile_begin(llg_ctx *c, int kernel_class) {
     LLG_GUARD(c);
     if (kernel_class < LLG_KCLASS_NONE || kernel_class > LLG_KCLASS_ARNOLDI)

@@ -82,6 +82,28 @@ __device__ __forceinline__ fpair &operator+=(fpair &a, fpair b) { return a = a +
 __device__ __forceinline__ fpair &operator-=(fpair &a, fpair b) { return a = a - b; }
 __device__ __forceinline__ fpair &operator*=(fpair &a, fpair b) { return a = a * b; }
 
+// a b + c d with one renormalisation: both leading products exact (fused multiply-add),
+// their sum by two-sum, every smaller term gathered in one FP32 correction
+__device__ __forceinline__ fpair fp_dot2(fpair a, fpair b, fpair c, fpair d) {
+    const float p = __fmul_rn(a.hi, b.hi), q = __fmul_rn(c.hi, d.hi);
+    const fpair s = fp_two_sum(p, q);
+    float t = __fmaf_rn(a.hi, b.hi, -p);
+    t = __fmaf_rn(a.hi, b.lo, t);
+    t = __fmaf_rn(a.lo, b.hi, t);
+    t = __fadd_rn(t, __fmaf_rn(c.hi, d.hi, -q));
+    t = __fmaf_rn(c.hi, d.lo, t);
+    t = __fmaf_rn(c.lo, d.hi, t);
+    return fp_fast_two_sum(s.hi, __fadd_rn(t, s.lo));
+}
+
+// complex product (the twiddle multiplications of the FFT stages): each part one fp_dot2
+__device__ __forceinline__ cfpair cmul(cfpair a, cfpair b) {
+    cfpair r;
+    r.x = fp_dot2(a.x, b.x, -a.y, b.y);
+    r.y = fp_dot2(a.x, b.y, a.y, b.x);
+    return r;
+}
+
 // conversions of per-element data (see convert.cuh for the FP32 <-> FP64 cases)
 template <> __device__ __forceinline__ fpair cvt<fpair, double>(double v) {
     const f32x2 s = split_f64(v);

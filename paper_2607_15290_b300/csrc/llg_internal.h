@@ -20,6 +20,13 @@ namespace llg {
 // grid's last wave still runs made the FP64 passes of mid-size grids up to 20% slower.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Hint: move [p, p + bytes) of global memory into L2 (one bulk prefetch; p 16-byte aligned,
+// bytes rounded down to a multiple of 16).  No completion to wait for, no effect on results.
+__device__ __forceinline__ void l2_prefetch_bulk(const void *p, unsigned long long bytes) {
+    const unsigned b = (unsigned)(bytes & ~15ull);
+    if (b) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(b) : "memory");
+}
+
 template <typename... KP, typename... A>
 inline cudaError_t launch_pdl(void (*k)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
     cudaLaunchConfig_t cfg = {};
@@ -193,6 +200,7 @@ void prof_discard(llg_ctx *c, size_t first, int min_tag);
 
 // spectral.cu
 llg_status autotune(llg_ctx *c, int prec_mask, std::string *report);
+llg_status set_axis_shape(llg_ctx *c, int fp32, int slot, const ColCfg &f);
 // FP64 Fourier transform along axis 1 (3D y) of every spectral column, no multiplier
 llg_status plain_axis_pass64(llg_ctx *c, int axis, bool forward);
 // every axis of the grid has a compile-time-length pass (the FP32-pair chains need one)

@@ -206,6 +206,8 @@ static cudaError_t launch_col_cfg(llg_ctx *c, int mode, const ColArgs<T> &a, int
 }
 
 template <typename T> static ColCfg slot_cfg(llg_ctx *c, int slot, int nl) {
+    // FP32-pair chains: the widest register tile (six blocks of 128 threads per SM)
+    if constexpr (is_fpair<T>::value) return col_default<T>(nl);
     const int pi = sizeof(T) == 4 ? 0 : 1;
     return c->tuned[pi] ? c->colcfg[pi][slot] : col_default<T>(nl);
 }
@@ -493,6 +495,32 @@ static llg_status tune_prec(llg_ctx *c, std::string *report) {
     cleanup();
     if (st == LLG_OK) c->tuned[pi] = true;
     return st;
+}
+
+template <typename T> static void fill_defaults(llg_ctx *c) {
+    const int pi = sizeof(T) == 4 ? 0 : 1;
+    const SpecGeom &g = c->geo;
+    for (int sl = 0; sl < NSLOT; ++sl) c->colcfg[pi][sl] = col_default<T>(sl == SLOT_Z ? g.n[2] : g.n[1]);
+    c->tuned[pi] = true;
+}
+
+// one slot's shape, set by hand (kept only if the tuner would consider it for this grid)
+llg_status set_axis_shape(llg_ctx *c, int fp32, int slot, const ColCfg &f) {
+    const SpecGeom &g = c->geo;
+    if (slot < 0 || slot >= NSLOT || (g.dim == 2) != (slot == SLOT_2D))
+        return set_error(c, LLG_ERR_INVALID_ARG, "axis shape: no such pass on this grid");
+    const int nl = slot == SLOT_Z ? g.n[2] : g.n[1];
+    const std::vector<ColCfg> cand = fp32 ? col_candidates<float>(c, nl) : col_candidates<double>(c, nl);
+    bool ok = false;
+    for (const ColCfg &q : cand) ok = ok || (q.kind == f.kind && q.E == f.E && q.TW == f.TW && q.CB == f.CB);
+    if (!ok) return set_error(c, LLG_ERR_INVALID_ARG, "axis shape: not a compiled shape for this line length");
+    const int pi = fp32 ? 0 : 1;
+    if (!c->tuned[pi]) {
+        if (fp32) fill_defaults<float>(c);
+        else fill_defaults<double>(c);
+    }
+    c->colcfg[pi][slot] = f;
+    return LLG_OK;
 }
 
 llg_status autotune(llg_ctx *c, int prec_mask, std::string *report) {

@@ -182,6 +182,28 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
     const C *const ibase = in ? in : a.spec;
     const long long irow0 = in ? 2 * (pair - in_pair0) : 2 * pair;
     const long long iS = in ? in_S : a.S;
+    constexpr bool NEED_M = (OUT == OUT_APPLY || OUT == OUT_FUSED || OUT == OUT_MATVEC || OUT == OUT_JT);
+    constexpr int XLO = OUT == OUT_APPLY ? 3 : 0;
+    constexpr int XHI = (OUT == OUT_APPLY || OUT == OUT_MATVEC || OUT == OUT_JT) ? 4 : (OUT == OUT_FUSED ? 3 : 0);
+    constexpr bool NEED_F = OUT == OUT_JT;
+    const NodalIO<TIn, TOut, T> &io = a.io;
+    {
+        // the epilogue's nodal planes (this block's nodes are contiguous in each plane) move
+        // towards L2 while the inverse transform runs: one bulk prefetch per plane
+        constexpr int NM = NEED_M ? 3 : 0, NXP = XHI - XLO, NF = NEED_F ? 4 : 0;
+        const long long j0 = pair0 * 2 * N;
+        if (tid < NM + NXP + NF && j0 < Nn) {
+            const long long cnt = (long long)2 * G * N < Nn - j0 ? (long long)2 * G * N : Nn - j0;
+            if (tid < NM) {
+                const nodal_t<T> *mp = OUT == OUT_JT ? io.mn : io.m;
+                l2_prefetch_bulk(mp + tid * Nn + j0, cnt * sizeof(nodal_t<T>));
+            } else if (tid < NM + NXP) {
+                l2_prefetch_bulk(io.x + (XLO + tid - NM) * Nn + j0, cnt * sizeof(TIn));
+            } else {
+                l2_prefetch_bulk(io.vf + (tid - NM - NXP) * Nn + j0, cnt * sizeof(nodal_t<T>));
+            }
+        }
+    }
     C v[E];
     if (valid) {
         if (kind < 2) {
@@ -216,13 +238,8 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
     }
     __syncthreads();
 
-    const NodalIO<TIn, TOut, T> &io = a.io;
     const T s = in_scale(io);
     constexpr int KC = sizeof(T) == 4 ? 6 : 3;
-    constexpr bool NEED_M = (OUT == OUT_APPLY || OUT == OUT_FUSED || OUT == OUT_MATVEC || OUT == OUT_JT);
-    constexpr int XLO = OUT == OUT_APPLY ? 3 : 0;
-    constexpr int XHI = (OUT == OUT_APPLY || OUT == OUT_MATVEC || OUT == OUT_JT) ? 4 : (OUT == OUT_FUSED ? 3 : 0);
-    constexpr bool NEED_F = OUT == OUT_JT;
     const int total = 2 * G * N;
     const long long j0 = pair0 * 2 * N;
     for (int base = tid; base < total; base += KC * nthr) {
@@ -311,8 +328,10 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
     }
 }
 
+// FP32-pair blocks (at most 3 x 128 threads) are held to 85 registers so that three blocks of
+// a 128-point row group fit an SM: the pair epilogue is latency-bound at two
 template <typename T, typename TIn, typename TOut, int LOGN, int OUT>
-__global__ void __launch_bounds__(512) row_inv_ct(RowArgs<T, TIn, TOut> a) {
+__global__ void __launch_bounds__(is_fpair<T>::value ? 384 : 512, is_fpair<T>::value ? 2 : 1) row_inv_ct(RowArgs<T, TIn, TOut> a) {
     pdl_wait();
     if (a.io.skip && *a.io.skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -372,8 +391,13 @@ __device__ __forceinline__ void col_ct_body(const ColArgs<T> &a, int bx, int by,
     for (int q = 0; q < E; ++q) p[q * step] = v[q];
 }
 
+template <typename T, int THREADS> struct ColMinBlocks {
+    static constexpr int value = is_fpair<T>::value ? (THREADS <= 128 ? 6 : (THREADS <= 256 ? 3 : 1))
+                                                    : ((sizeof(T) == 4 && THREADS <= 512) ? 2 : 1);
+};
+
 template <typename T, int LOGN, int E, int TW, int MODE, bool DB>
-__global__ void __launch_bounds__(TW *((1 << LOGN) / E), (sizeof(T) == 4 && TW * ((1 << LOGN) / E) <= 512) ? 2 : 1)
+__global__ void __launch_bounds__(TW *((1 << LOGN) / E), (ColMinBlocks<T, TW * ((1 << LOGN) / E)>::value))
     col_ct(ColArgs<T> a) {
     pdl_wait();
     if (a.skip && *a.skip) return;
