@@ -54,10 +54,10 @@ def peaks():
 ARNOLDI_TRAFFIC_BYTES = 371.3e6
 ARNOLDI_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 90 non-empty "
                         "arnoldi_pass launches of this workload (exact-count kernels, fused reduction)")
-# the same for the FP32-pair passes (arnoldi_pass_pair), 90 launches of this workload
-PAIR_TRAFFIC_BYTES = 394.5e6
-PAIR_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 90 arnoldi_pass_pair "
-                     "launches of this workload (profiles/gs_pass_pair_128cube_dram.md)")
+# the same for the FP32-pair passes (gs_pass_staged), 90 launches of this workload
+PAIR_TRAFFIC_BYTES = 392.6e6
+PAIR_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 90 gs_pass_staged "
+                     "launches of this workload (profiles/gs_pass_staged_128cube_dram.md)")
 
 
 def aggregate_over_ranks(dist, ms, counts, device):
@@ -457,7 +457,8 @@ def main():
                 "frac": achieved / pk["hbm_gbs"], "traffic": PAIR_TRAFFIC_BYTES if args.n == 128 else None,
                 "traffic_note": PAIR_TRAFFIC_NOTE,
                 "algorithmic_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
-                "kernel": "arnoldi_pass_pair (CGS2 multi-dot/update, FP32-pair arithmetic on a planar-pair basis)",
+                "kernel": "gs_pass_staged (CGS2 multi-dot/update, FP32-pair arithmetic on a planar-pair basis, "
+                          "operands staged in shared memory by bulk copies)",
                 "launches": prof["launches"], "avg_launch_ms": avg_ms,
                 "fp64_equivalent_tflops": prof["flops"] / (prof["ms"] / 1e3) / 1e12,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" + (" (fallback)" if pk.get("fallback") else "")}
