@@ -2,18 +2,19 @@
 // arithmetic and data layout as arnoldi_pass_pair in krylov.cu), with their operands staged
 // in shared memory by bulk copies.
 //
-// Each persistent block walks its share of the vectors in chunks through a two-stage ring:
-// while it computes on chunk k from shared memory, the bulk copies of chunk k+1 (the FP32
-// hi plane of w, in pass C also its lo plane, the FP64 first basis vector and the hi and lo
-// planes of every later one; cp.async.bulk, completion on an mbarrier) are in flight.  The
-// loads then no longer hold registers while they wait, so the block keeps many bytes in
-// flight at any occupancy; the register form of these passes waits on its loads (long-
-// scoreboard stalls) at 56-70% of the memory floor.
+// Each persistent block walks its share of the vectors in chunks through a ring of NS stages
+// in shared memory, run as a producer/consumer pipeline: one producer warp fills a stage with
+// the bulk copies of a chunk (the FP32 hi plane of w, in pass C also its lo plane, the FP64
+// first basis vector and the hi and lo planes of every later one; cp.async.bulk, completion
+// on the stage's "full" mbarrier) as soon as the consumers have released it (its "empty"
+// mbarrier, one arrival per consumer warp); eight consumer warps wait on "full", compute, and
+// release.  No block-wide barrier sits in the loop, so warps drift by up to the ring's depth
+// instead of meeting after every chunk, and NS - 1 chunks stay in flight per block.
 //
 // Every mbarrier wait is bounded (about 1 s of clock).  A wait that runs out raises the
-// error word in host-mapped memory (the host reports LLG_ERR_TIMEOUT at its next check),
-// waits (bounded) for the block's copies in flight, and the block still stores its partial
-// sums and counts its arrival, so the pass's last-block bookkeeping stays consistent.
+// error word in host-mapped memory (the host reports LLG_ERR_TIMEOUT at its next check); the
+// warp stops, the block waits (bounded) for every copy it issued, and still stores its
+// partial sums and counts its arrival, so the pass's last-block bookkeeping stays consistent.
 #include <algorithm>
 #include "spectral_kernels.cuh"
 #include "krylov_dev.cuh"
@@ -26,8 +27,18 @@ namespace gst {
 
 using namespace llg::tma;
 
-constexpr int NT = 256;                  // threads per block
-constexpr int STAGE_TARGET = 48 * 1024;  // bytes per stage (two stages per block)
+constexpr int NCW = 8;                    // consumer warps
+constexpr int NC = NCW * 32;              // consumer threads (RB_THREADS: the block reduction's width)
+constexpr int NT = NC + 32;               // + one producer warp
+static_assert(NC == RB_THREADS, "consumer threads = reduction width");
+
+// ring shape: up to 12 basis vectors two blocks per SM with three 32 KB stages each; beyond
+// that (more registers a thread) one block per SM with four 48 KB stages
+template <int MAXV> struct Ring {
+    static constexpr int BLOCKS = MAXV <= 12 ? 2 : 1;
+    static constexpr int NS = MAXV <= 12 ? 3 : 4;
+    static constexpr int TARGET = MAXV <= 12 ? 32 * 1024 : 48 * 1024;
+};
 
 // bytes staged per vector element: w hi (+ w lo in pass C), V_0 (FP64), 8 per later vector
 __host__ __device__ constexpr int elem_bytes(int nv, int mode) { return 4 + (mode == PASS_UPD_NRM ? 4 : 0) + 8 * nv; }
@@ -41,19 +52,20 @@ struct ChunkLayout {
 };
 
 template <int MAXV, int MODE>
-__global__ void __launch_bounds__(NT, 2) gs_pass_staged(const double *__restrict__ V, long long ldv, int nv, GmresDev *gd,
-                                                      const float *w_hi, const float *w_lo, float *o_hi, float *o_lo,
-                                                      long long n, ChunkLayout lay, double *__restrict__ partials,
-                                                      volatile int *err) {
+__global__ void __launch_bounds__(NT, Ring<MAXV>::BLOCKS)
+    gs_pass_staged(const double *__restrict__ V, long long ldv, int nv, GmresDev *gd, const float *w_hi,
+                   const float *w_lo, float *o_hi, float *o_lo, long long n, ChunkLayout lay,
+                   double *__restrict__ partials, volatile int *err) {
+    constexpr int NS = Ring<MAXV>::NS;
     pdl_wait();
     if (gd->done) return;
     constexpr bool WLO = MODE == PASS_UPD_NRM;
     extern __shared__ __align__(128) unsigned char smraw[];
     unsigned char *ring = smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u);
-    __shared__ __align__(8) unsigned long long bar[2];
-    __shared__ int s_ok;
+    __shared__ __align__(8) unsigned long long full[NS], empty[NS];
     __shared__ f32x2 coef[MAXV];
-    const int tid = threadIdx.x;
+    __shared__ double red[NCW][MAXV];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int CH = lay.CH;
     const size_t SB = lay.stage_bytes(nv, MODE);
     if (tid < nv) {
@@ -61,98 +73,129 @@ __global__ void __launch_bounds__(NT, 2) gs_pass_staged(const double *__restrict
         coef[tid] = split_f64(h * gd->scale[tid]);
     }
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int st = 0; st < NS; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], NCW);
+        }
         mbar_init_fence();
     }
     __syncthreads();
     const long long nchunks = (n + CH - 1) / CH;
-    // stage pointers
+    const long long first = blockIdx.x, stride = gridDim.x;
     auto w_h_s = [&](int st) { return reinterpret_cast<float *>(ring + st * SB); };
     auto w_l_s = [&](int st) { return w_h_s(st) + CH; };
     auto v0_s = [&](int st) { return reinterpret_cast<double *>(w_h_s(st) + (WLO ? 2 : 1) * CH); };
     auto vh_s = [&](int st, int i) { return reinterpret_cast<float *>(v0_s(st) + CH) + (size_t)2 * (i - 1) * CH; };
-    auto issue = [&](long long chunk, int st) {
-        const long long e0 = chunk * CH;
-        const unsigned len = (unsigned)std::min<long long>(CH, n - e0);
-        mbar_expect_tx(&bar[st], len * (unsigned)elem_bytes(nv, MODE));
-        bulk_load(w_h_s(st), w_hi + e0, len * 4u, &bar[st]);
-        if (WLO) bulk_load(w_l_s(st), w_lo + e0, len * 4u, &bar[st]);
-        bulk_load(v0_s(st), V + e0, len * 8u, &bar[st]);
-        for (int i = 1; i < nv; ++i) {
-            const float *b = reinterpret_cast<const float *>(V + i * ldv);
-            bulk_load(vh_s(st, i), b + e0, len * 4u, &bar[st]);
-            bulk_load(vh_s(st, i) + CH, b + n + e0, len * 4u, &bar[st]);
-        }
-    };
+    bool failed = false;
     f32x2 acc[MAXV];
 #pragma unroll
     for (int i = 0; i < MAXV; ++i) acc[i] = f32x2{0.0f, 0.0f};
-    const long long first = blockIdx.x, stride = gridDim.x;
-    if (tid == 0 && first < nchunks) issue(first, 0);
-    bool failed = false;
-    int k = 0;
-    for (long long chunk = first; chunk < nchunks; chunk += stride, ++k) {
-        const int st = k & 1;
-        const unsigned parity = (unsigned)((k >> 1) & 1);
-        if (tid == 0) {
-            // the other stage was last read in iteration k - 1, which every thread has left
-            if (chunk + stride < nchunks) issue(chunk + stride, st ^ 1);
-            s_ok = mbar_wait_bounded(&bar[st], parity) ? 1 : 0;
-        }
-        __syncthreads();
-        if (!s_ok) { failed = true; break; }
-        if (__syncthreads_or(mbar_wait_bounded(&bar[st], parity) ? 0 : 1)) { failed = true; break; }
-        const long long e0 = chunk * CH;
-        const int len = (int)std::min<long long>(CH, n - e0);
-        const float *wh = w_h_s(st), *wl = w_l_s(st);
-        const double *v0 = v0_s(st);
-        for (int r = tid; r < len; r += NT) {
-            const f32x2 w{wh[r], WLO ? wl[r] : 0.0f};
-            f32x2 v[MAXV];
-            v[0] = split_f64(v0[r]);
-#pragma unroll
-            for (int i = 1; i < MAXV; ++i)
-                if (i < nv) {
-                    const float *b = vh_s(st, i);
-                    v[i] = f32x2{b[r], b[CH + r]};
-                }
-            if (MODE == PASS_DOT) {
-#pragma unroll
-                for (int i = 0; i < MAXV; ++i)
-                    if (i < nv) fma_acc(v[i], w, acc[i]);
-            } else {
-                f32x2 u{0.0f, 0.0f};
-#pragma unroll
-                for (int i = 0; i < MAXV; ++i)
-                    if (i < nv) fma_acc(coef[i], v[i], u);
-                const f32x2 wn = sub_pair(w, u);
-                o_hi[e0 + r] = wn.hi;
-                o_lo[e0 + r] = wn.lo;
-                if (MODE == PASS_UPD_DOT) {
-#pragma unroll
-                    for (int i = 0; i < MAXV; ++i)
-                        if (i < nv) fma_acc(v[i], wn, acc[i]);
-                } else {
-                    fma_acc(wn, wn, acc[0]);
+
+    if (warp == NCW) {
+        // producer: lane 0 arms the stage's barrier, then the lanes share its copies
+        long long issued = 0;
+        for (long long chunk = first; chunk < nchunks; chunk += stride, ++issued) {
+            const int st = (int)(issued % NS);
+            if (issued >= NS) {
+                // the consumers released this stage's previous chunk
+                const bool ok = mbar_wait_bounded(&empty[st], (unsigned)(((issued / NS) - 1) & 1));
+                if (__any_sync(0xffffffffu, !ok)) { failed = true; break; }
+            }
+            const long long e0 = chunk * CH;
+            const unsigned len = (unsigned)std::min<long long>(CH, n - e0);
+            if (lane == 0) mbar_expect_tx(&full[st], len * (unsigned)elem_bytes(nv, MODE));
+            __syncwarp();
+            // copy q: 0 w hi, 1 w lo (pass C), 2 V_0, 3 + 2 (i - 1) (+1) the hi (lo) plane of V_i
+            for (int q = lane; q < 3 + 2 * (nv - 1); q += 32) {
+                if (q == 0) bulk_load(w_h_s(st), w_hi + e0, len * 4u, &full[st]);
+                else if (q == 1) { if (WLO) bulk_load(w_l_s(st), w_lo + e0, len * 4u, &full[st]); }
+                else if (q == 2) bulk_load(v0_s(st), V + e0, len * 8u, &full[st]);
+                else {
+                    const int i = 1 + (q - 3) / 2, lo = (q - 3) & 1;
+                    const float *b = reinterpret_cast<const float *>(V + i * ldv) + (lo ? n : 0);
+                    bulk_load(vh_s(st, i) + (lo ? CH : 0), b + e0, len * 4u, &full[st]);
                 }
             }
         }
-        __syncthreads();   // this stage is free for the copies of chunk k + 2
-    }
-    if (failed && tid == 0) {
-        *err = 1;
-        __threadfence_system();
+        if (failed && lane == 0) {
+            *err = 1;
+            __threadfence_system();
+        }
         // copies still in flight land in this block's shared memory: wait for them (bounded)
-        for (int q = 0; q < 2; ++q) {
-            const long long c = first + (long long)(k + q) * stride;
-            if (c < nchunks) mbar_wait_bounded(&bar[(k + q) & 1], (unsigned)(((k + q) >> 1) & 1));
+        if (lane == 0)
+            for (long long k = std::max(0LL, issued - NS); k < issued; ++k)
+                mbar_wait_bounded(&full[k % NS], (unsigned)((k / NS) & 1));
+    } else {
+        long long k = 0;
+        for (long long chunk = first; chunk < nchunks; chunk += stride, ++k) {
+            const int st = (int)(k % NS);
+            if (__any_sync(0xffffffffu, !mbar_wait_bounded(&full[st], (unsigned)((k / NS) & 1)))) {
+                failed = true;
+                break;
+            }
+            const long long e0 = chunk * CH;
+            const int len = (int)std::min<long long>(CH, n - e0);
+            const float *wh = w_h_s(st), *wl = w_l_s(st);
+            const double *v0 = v0_s(st);
+            for (int r = tid; r < len; r += NC) {
+                const f32x2 w{wh[r], WLO ? wl[r] : 0.0f};
+                f32x2 v[MAXV];
+                v[0] = split_f64(v0[r]);
+#pragma unroll
+                for (int i = 1; i < MAXV; ++i)
+                    if (i < nv) {
+                        const float *b = vh_s(st, i);
+                        v[i] = f32x2{b[r], b[CH + r]};
+                    }
+                if (MODE == PASS_DOT) {
+#pragma unroll
+                    for (int i = 0; i < MAXV; ++i)
+                        if (i < nv) fma_acc(v[i], w, acc[i]);
+                } else {
+                    f32x2 u{0.0f, 0.0f};
+#pragma unroll
+                    for (int i = 0; i < MAXV; ++i)
+                        if (i < nv) fma_acc(coef[i], v[i], u);
+                    const f32x2 wn = sub_pair(w, u);
+                    o_hi[e0 + r] = wn.hi;
+                    o_lo[e0 + r] = wn.lo;
+                    if (MODE == PASS_UPD_DOT) {
+#pragma unroll
+                        for (int i = 0; i < MAXV; ++i)
+                            if (i < nv) fma_acc(v[i], wn, acc[i]);
+                    } else {
+                        fma_acc(wn, wn, acc[0]);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[st])) : "memory");
+        }
+        if (failed && lane == 0) {
+            *err = 1;
+            __threadfence_system();
         }
     }
-    double accd[MAXV];
+    // block reduction over the consumer warps (the producer's accumulators are zero)
+    const int nout = MODE == PASS_UPD_NRM ? 1 : nv;
+    if (warp < NCW) {
 #pragma unroll
-    for (int i = 0; i < MAXV; ++i) accd[i] = failed ? 0.0 : pair_to_f64(acc[i]);
-    block_reduce_store<MAXV>(accd, MODE == PASS_UPD_NRM ? 1 : nv, partials + (long long)blockIdx.x * RB_STRIDE);
+        for (int i = 0; i < MAXV; ++i) {
+            if (i < nout) {
+                double v = failed ? 0.0 : pair_to_f64(acc[i]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) red[warp][i] = v;
+            }
+        }
+    }
+    __syncthreads();
+    double *out = partials + (long long)blockIdx.x * RB_STRIDE;
+    for (int i = tid; i < nout; i += NT) {
+        double t = 0.0;
+        for (int w = 0; w < NCW; ++w) t += red[w][i];
+        out[i] = t;
+    }
     if (last_block_arrived(&gd->arrived)) arnoldi_finish(partials, gridDim.x, nv, gd, MODE, nv - 1);
 }
 
@@ -160,9 +203,9 @@ template <int MAXV, int MODE>
 static cudaError_t launch_one(llg_ctx *c, const double *V, long long ldv, int nv, const float *wh, const float *wl,
                               float *oh, float *ol, long long n) {
     ChunkLayout lay;
-    lay.CH = std::max(4, (STAGE_TARGET / elem_bytes(nv, MODE)) / 4 * 4);
+    lay.CH = std::max(4, (Ring<MAXV>::TARGET / elem_bytes(nv, MODE)) / 4 * 4);
     if (lay.CH > n) lay.CH = (int)((n + 3) / 4 * 4);
-    const size_t sm = 2 * lay.stage_bytes(nv, MODE) + 128;
+    const size_t sm = Ring<MAXV>::NS * lay.stage_bytes(nv, MODE) + 128;
     auto k = gs_pass_staged<MAXV, MODE>;
     cudaError_t e = set_smem(k, sm);
     if (e != cudaSuccess) return e;
