@@ -37,10 +37,12 @@ struct TileMap {
     int tiles_x, ntiles, axis_z;
 };
 
-template <int LOGN, int TW, int MODE>
-__global__ void __launch_bounds__(TW *((1 << LOGN) / 8)) col_tma_kernel(const __grid_constant__ CUtensorMap map,
+// E points of a line per thread: 8 (radix-8 stages) or 16 (radix-16 stages: half the
+// shared-memory exchanges of a 256-point line)
+template <int LOGN, int TW, int MODE, int E>
+__global__ void __launch_bounds__(TW *((1 << LOGN) / E)) col_tma_kernel(const __grid_constant__ CUtensorMap map,
                                                                         ColArgs<float> a, TileMap tm, volatile int *err) {
-    constexpr int N = 1 << LOGN, E = 8, P = N / E;
+    constexpr int N = 1 << LOGN, P = N / E, LR = E == 16 ? 4 : 3;
     constexpr int TILE = N * TW;                         // float2 elements
     constexpr unsigned BYTES = TILE * sizeof(float2);
     using L = ct::ColL<TW>;
@@ -106,13 +108,13 @@ __global__ void __launch_bounds__(TW *((1 << LOGN) / 8)) col_tma_kernel(const __
             // round trip: stage 0 stores into the exchange tile X, so no thread waits for the
             // others' loads of T, and the two buffers alternate with one barrier per stage
             float2 *X = ring + STAGES * TILE + c;
-            ct::fft<LOGN, E, -1, L, 1, true>(v, T, X, t, a.tw);
+            ct::fft<LOGN, E, -1, L, 1, true, LR>(v, T, X, t, a.tw);
             ct::apply_symbol<float, LOGN, E, L>(v, a, bx * TW + c, b, t);
-            ct::fft<LOGN, E, +1, L, ct::FreeBuf<LOGN, E, 1>::value, true>(v, T, X, t, a.tw);
+            ct::fft<LOGN, E, +1, L, ct::FreeBuf<LOGN, E, 1, LR>::value, true, LR>(v, T, X, t, a.tw);
         } else {
-            if constexpr ((MODE & 1) != 0) ct::fft<LOGN, E, -1, L, 0, false>(v, T, T, t, a.tw);
+            if constexpr ((MODE & 1) != 0) ct::fft<LOGN, E, -1, L, 0, false, LR>(v, T, T, t, a.tw);
             if constexpr ((MODE & 4) != 0) ct::apply_symbol<float, LOGN, E, L>(v, a, bx * TW + c, b, t);
-            if constexpr ((MODE & 2) != 0) ct::fft<LOGN, E, +1, L, 0, false>(v, T, T, t, a.tw);
+            if constexpr ((MODE & 2) != 0) ct::fft<LOGN, E, +1, L, 0, false, LR>(v, T, T, t, a.tw);
         }
         __syncthreads();   // every load of the last stage precedes the write-back
 #pragma unroll
@@ -166,11 +168,11 @@ bool available(const llg_ctx *c, int nl) {
     return c->dprog != nullptr && (nl == 128 || nl == 256) && encoder() != nullptr;
 }
 
-template <int LOGN, int TW, int MODE>
+template <int LOGN, int TW, int MODE, int E>
 static cudaError_t launch_one(llg_ctx *c, const CUtensorMap &map, const ColArgs<float> &a, TileMap tm) {
-    constexpr int N = 1 << LOGN, threads = TW * (N / 8);
+    constexpr int N = 1 << LOGN, threads = TW * (N / E);
     constexpr size_t sm = (size_t)tiles_held(MODE) * N * TW * sizeof(float2) + 128;
-    auto k = col_tma_kernel<LOGN, TW, MODE>;
+    auto k = col_tma_kernel<LOGN, TW, MODE, E>;
     cudaError_t e = set_smem(k, sm);
     if (e != cudaSuccess) return e;
     int per = 0, dev = 0, sms = 0;
@@ -182,18 +184,24 @@ static cudaError_t launch_one(llg_ctx *c, const CUtensorMap &map, const ColArgs<
     return launch_pdl(k, dim3(blocks), dim3(threads), sm, c->stream, map, a, tm, c->dprog + KERR_WORD);
 }
 
-template <int LOGN, int TW>
+template <int LOGN, int TW, int E>
 static cudaError_t launch_mode(llg_ctx *c, int mode, const CUtensorMap &map, const ColArgs<float> &a, TileMap tm) {
-    if (mode == 1) return launch_one<LOGN, TW, 1>(c, map, a, tm);
-    if (mode == 2) return launch_one<LOGN, TW, 2>(c, map, a, tm);
-    if (mode == 7) return launch_one<LOGN, TW, 7>(c, map, a, tm);
+    if (mode == 1) return launch_one<LOGN, TW, 1, E>(c, map, a, tm);
+    if (mode == 2) return launch_one<LOGN, TW, 2, E>(c, map, a, tm);
+    if (mode == 7) return launch_one<LOGN, TW, 7, E>(c, map, a, tm);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t col_launch(llg_ctx *c, int mode, const ColArgs<float> &a, int batches, int TW) {
+template <int LOGN, int TW>
+static cudaError_t launch_e(llg_ctx *c, int mode, int E, const CUtensorMap &map, const ColArgs<float> &a, TileMap tm) {
+    return E == 16 ? launch_mode<LOGN, TW, 16>(c, mode, map, a, tm) : launch_mode<LOGN, TW, 8>(c, mode, map, a, tm);
+}
+
+cudaError_t col_launch(llg_ctx *c, int mode, const ColArgs<float> &a, int batches, int TW, int E) {
     const SpecGeom &g = c->geo;
     EncodeTiled enc = encoder();
-    if (!enc || !c->dprog || (a.nl != 128 && a.nl != 256) || (TW != 8 && TW != 16)) return cudaErrorNotSupported;
+    if (!enc || !c->dprog || (a.nl != 128 && a.nl != 256) || (TW != 8 && TW != 16) || (E != 8 && E != 16))
+        return cudaErrorNotSupported;
     // the spectrum as a 3D tensor of floats: (2 S, n1, n2), rows of S complex slots
     const bool axis_z = a.ls != (long long)g.S;   // the z pass steps n1 S between line points
     const cuuint64_t dims[3] = {(cuuint64_t)(2 * g.S), (cuuint64_t)g.n[1], (cuuint64_t)(g.dim == 3 ? g.n[2] : 1)};
@@ -209,8 +217,8 @@ cudaError_t col_launch(llg_ctx *c, int mode, const ColArgs<float> &a, int batche
     tm.tiles_x = g.S / TW;
     tm.ntiles = tm.tiles_x * batches;
     tm.axis_z = axis_z ? 1 : 0;
-    if (a.nl == 128) return TW == 16 ? launch_mode<7, 16>(c, mode, map, a, tm) : launch_mode<7, 8>(c, mode, map, a, tm);
-    return TW == 16 ? launch_mode<8, 16>(c, mode, map, a, tm) : launch_mode<8, 8>(c, mode, map, a, tm);
+    if (a.nl == 128) return TW == 16 ? launch_e<7, 16>(c, mode, E, map, a, tm) : launch_e<7, 8>(c, mode, E, map, a, tm);
+    return TW == 16 ? launch_e<8, 16>(c, mode, E, map, a, tm) : launch_e<8, 8>(c, mode, E, map, a, tm);
 }
 
 }  // namespace tma

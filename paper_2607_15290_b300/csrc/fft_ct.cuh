@@ -25,14 +25,17 @@
 namespace llg {
 namespace ct {
 
-template <int LOGN, int E>
+// stages of radix 2^LR (8, or 16 for lines held 16 points a thread), then one stage for the
+// remaining bits
+template <int LOGN, int E, int LR = 3>
 struct Plan {
     static constexpr int N = 1 << LOGN;
     static constexpr int P = N / E;
-    static constexpr int NST = (LOGN + 2) / 3;
-    static constexpr int lr(int s) { return s < LOGN / 3 ? 3 : LOGN % 3; }
-    static constexpr int Ns(int s) { return 1 << (3 * s); }
+    static constexpr int NST = (LOGN + LR - 1) / LR;
+    static constexpr int lr(int s) { return s < LOGN / LR ? LR : LOGN % LR; }
+    static constexpr int Ns(int s) { return 1 << (LR * s); }
     static_assert(E == 8 || E == 16, "radix-8 stages need E >= 8");
+    static_assert((1 << LR) <= E && (LR == 3 || LR == 4), "a stage's radix is 8 or 16, at most E");
     static_assert(LOGN >= 6 && LOGN <= 10, "compile-time plans cover 64..1024");
 };
 
@@ -65,9 +68,9 @@ __device__ __forceinline__ C tw_load(const C *__restrict__ tw, int i) {
 
 // one Stockham stage S.  DB: two exchange buffers (one barrier per stage); without
 // it buf0 == buf1 and a barrier also separates this stage's loads from its stores.
-template <int LOGN, int E, int SIGN, class L, int S, int PAR, bool DB, typename C>
+template <int LOGN, int E, int SIGN, class L, int S, int PAR, bool DB, int LR, typename C>
 __device__ __forceinline__ void stage(C (&a)[E], C *buf0, C *buf1, int t, const C *__restrict__ tw) {
-    using PL = Plan<LOGN, E>;
+    using PL = Plan<LOGN, E, LR>;
     constexpr int R = 1 << PL::lr(S), Ns = PL::Ns(S), Q = E / R, P = PL::P, N = PL::N;
     constexpr bool last = S == PL::NST - 1;
     constexpr int TWS = N / (R * Ns);   // twiddle index scale
@@ -102,7 +105,8 @@ __device__ __forceinline__ void stage(C (&a)[E], C *buf0, C *buf1, int t, const 
         }
         if constexpr (R == 2) dft2<SIGN>(b[0], b[1]);
         else if constexpr (R == 4) dft4<SIGN>(b[0], b[1], b[2], b[3]);
-        else dft8<SIGN>(b);
+        else if constexpr (R == 8) dft8<SIGN>(b);
+        else dft16<SIGN>(b);
         if constexpr (last) {
 #pragma unroll
             for (int r = 0; r < R; ++r) a[q + r * Q] = b[r];
@@ -114,16 +118,16 @@ __device__ __forceinline__ void stage(C (&a)[E], C *buf0, C *buf1, int t, const 
             }
         }
     }
-    if constexpr (!last) stage<LOGN, E, SIGN, L, S + 1, PAR, DB>(a, buf0, buf1, t, tw);
+    if constexpr (!last) stage<LOGN, E, SIGN, L, S + 1, PAR, DB, LR>(a, buf0, buf1, t, tw);
 }
 
 // Length-2^LOGN DFT (sign SIGN, unnormalised) of the line whose elements t + P s
 // thread t holds in a[s], in place.  Stage S stores into buffer (S + PAR) & 1; the
 // caller makes sure no thread still reads the buffer stage 0 writes (PAR picks it).
 // Every thread of the block calls this (it contains barriers).
-template <int LOGN, int E, int SIGN, class L, int PAR = 0, bool DB = true, typename C>
+template <int LOGN, int E, int SIGN, class L, int PAR = 0, bool DB = true, int LR = 3, typename C>
 __device__ __forceinline__ void fft(C (&a)[E], C *buf0, C *buf1, int t, const C *__restrict__ tw) {
-    stage<LOGN, E, SIGN, L, 0, PAR, DB>(a, buf0, buf1, t, tw);
+    stage<LOGN, E, SIGN, L, 0, PAR, DB, LR>(a, buf0, buf1, t, tw);
 }
 
 // ---------------------------------------------------------------- two adjacent FP32 lines
@@ -200,8 +204,8 @@ __device__ __forceinline__ void fft2(float2 (&a)[E], float2 (&b)[E], float2 *buf
 
 // the buffer that no stage of a transform with parity PAR reads last, free for the
 // caller right after the transform returns
-template <int LOGN, int E, int PAR>
-struct FreeBuf { static constexpr int value = (Plan<LOGN, E>::NST - 1 + PAR) & 1; };
+template <int LOGN, int E, int PAR, int LR = 3>
+struct FreeBuf { static constexpr int value = (Plan<LOGN, E, LR>::NST - 1 + PAR) & 1; };
 
 }  // namespace ct
 }  // namespace llg

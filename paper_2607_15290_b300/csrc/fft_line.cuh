@@ -65,6 +65,37 @@ template <int SIGN, typename C> __device__ __forceinline__ void dft8(C (&a)[8]) 
     a[3] = cadd(e3, w3); a[7] = csub(e3, w3);
 }
 
+// 16-point DFT as 4 x 4: DFTs of the four decimated sets {n2, n2 + 4, n2 + 8, n2 + 12}, the
+// twiddles W16^(n2 k1), then DFTs across n2; output k1 + 4 k2 in natural order
+template <int SIGN, typename C> __device__ __forceinline__ void dft16(C (&a)[16]) {
+    using T = decltype(C::x);
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;   // cos, sin of pi/8
+    const T h = (T)0.70710678118654752440;
+    C y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        C p0 = a[n2], p1 = a[n2 + 4], p2 = a[n2 + 8], p3 = a[n2 + 12];
+        dft4<SIGN>(p0, p1, p2, p3);
+        y[n2][0] = p0; y[n2][1] = p1; y[n2][2] = p2; y[n2][3] = p3;
+    }
+    // W16^m = cos(2 pi m / 16) + SIGN i sin(2 pi m / 16)
+    y[1][1] = cmul(y[1][1], cmk<C>(c1, sgn<SIGN>(s1)));
+    y[1][2] = cmul(y[1][2], cmk<C>(h, sgn<SIGN>(h)));
+    y[1][3] = cmul(y[1][3], cmk<C>(s1, sgn<SIGN>(c1)));
+    y[2][1] = cmul(y[2][1], cmk<C>(h, sgn<SIGN>(h)));
+    y[2][2] = cmul_i<SIGN>(y[2][2]);
+    y[2][3] = cmul(y[2][3], cmk<C>(-h, sgn<SIGN>(h)));
+    y[3][1] = cmul(y[3][1], cmk<C>(s1, sgn<SIGN>(c1)));
+    y[3][2] = cmul(y[3][2], cmk<C>(-h, sgn<SIGN>(h)));
+    y[3][3] = cmul(y[3][3], cmk<C>(-c1, -sgn<SIGN>(s1)));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        C q0 = y[0][k1], q1 = y[1][k1], q2 = y[2][k1], q3 = y[3][k1];
+        dft4<SIGN>(q0, q1, q2, q3);
+        a[k1] = q0; a[k1 + 4] = q1; a[k1 + 8] = q2; a[k1 + 12] = q3;
+    }
+}
+
 // Shared-memory index of element e of a line: rows use a padded contiguous
 // layout (one pad slot every 8 elements kills the stride-R bank conflicts of
 // the first stages); column tiles interleave TW lines element by element.

@@ -152,7 +152,8 @@ template <typename T> static std::vector<ColCfg> col_candidates(const llg_ctx *c
     }
     if (sizeof(T) == 4 && tma::available(c, nl)) {
         // persistent kernels fed by the tensor memory accelerator
-        for (int TW : {8, 16}) v.push_back({4, 8, TW, 0});
+        for (int TW : {8, 16})
+            for (int E : {8, 16}) v.push_back({4, E, TW, 0});
     }
     if (sizeof(T) == 4 && nl >= 64) {
         for (auto &sc : kStaged) {
@@ -175,7 +176,7 @@ template <typename T> static ColCfg col_default(int nl) {
 template <typename T>
 static cudaError_t launch_col_cfg(llg_ctx *c, int mode, const ColArgs<T> &a, int batches, const ColCfg &cfg) {
     if (cfg.kind == 4) {
-        if constexpr (sizeof(T) == 4) return tma::col_launch(c, mode, a, batches, cfg.TW);
+        if constexpr (sizeof(T) == 4) return tma::col_launch(c, mode, a, batches, cfg.TW, cfg.E);
         return cudaErrorInvalidValue;
     }
     if (cfg.kind == 1) {
@@ -412,7 +413,8 @@ static std::string cfg_name(const ColCfg &f) {
     char b[64];
     if (f.kind == 0) snprintf(b, sizeof b, "register(E%d,TW%d)", f.E, f.TW);
     else if (f.kind == 3) snprintf(b, sizeof b, "paired(E%d,TW%d)", f.E, f.TW);
-    else if (f.kind == 4) snprintf(b, sizeof b, "tma(TW%d)", f.TW);
+    else if (f.kind == 4 && f.E == 8) snprintf(b, sizeof b, "tma(TW%d)", f.TW);
+    else if (f.kind == 4) snprintf(b, sizeof b, "tma(E%d,TW%d)", f.E, f.TW);
     else snprintf(b, sizeof b, "staged(TW%d,CB%d)", f.TW, f.CB);
     return b;
 }

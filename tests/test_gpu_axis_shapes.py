@@ -17,13 +17,14 @@ def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
 
 
-@pytest.mark.parametrize("shapes", [
-    {"y-forward": "register(E8,TW16)", "z": "tma(TW8)", "y-inverse": "register(E8,TW16)"},
-    {"y-forward": "tma(TW16)", "z": "paired(E8,TW16)", "y-inverse": "staged(TW16,CB8)"},
-    {"z": "staged(TW32,CB16)"},
-], ids=["live-128", "mixed", "z-only"])
-def test_fixed_shapes_match_oracle(shapes):
-    n = (128, 128, 128)
+@pytest.mark.parametrize("n,shapes", [
+    ((128, 128, 128), {"y-forward": "register(E8,TW16)", "z": "tma(TW8)", "y-inverse": "register(E8,TW16)"}),
+    ((128, 128, 128), {"y-forward": "tma(TW16)", "z": "paired(E8,TW16)", "y-inverse": "staged(TW16,CB8)"}),
+    ((128, 128, 128), {"z": "staged(TW32,CB16)"}),
+    ((128, 128, 128), {"y-forward": "tma(E16,TW8)", "z": "tma(E16,TW16)", "y-inverse": "tma(E16,TW16)"}),
+    ((64, 256, 256), {"y-forward": "tma(E16,TW16)", "z": "tma(E16,TW8)", "y-inverse": "tma(E16,TW8)"}),
+], ids=["live-128", "mixed", "z-only", "radix16-128", "radix16-256"])
+def test_fixed_shapes_match_oracle(n, shapes):
     og = O.Grid(n)
     ctx = L.Context(n)
     for slot, shape in shapes.items():
