@@ -74,4 +74,74 @@ __device__ __forceinline__ f32x2 sub_pair(const f32x2 &a, const f32x2 &b) {
 // hi + lo as a double (both widened exactly on the integer pipes, one FP64 addition)
 __device__ __forceinline__ double pair_to_f64(const f32x2 &a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
 
+// ---- two FP32 pairs in packed registers: the same transformations on two independent values
+// at once with the packed FP32 instructions (add/sub/mul/fma .f32x2, round to nearest): half
+// the instructions, and two independent dependency chains per instruction.  Lane 0 of each
+// 64-bit register belongs to the first value, lane 1 to the second.
+typedef unsigned long long f32v2;
+struct f32x2v2 {
+    f32v2 hi, lo;
+};
+
+__device__ __forceinline__ f32v2 v2_pack(float a, float b) {
+    f32v2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void v2_unpack(f32v2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f32v2 v2_add(f32v2 a, f32v2 b) {
+    f32v2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32v2 v2_sub(f32v2 a, f32v2 b) {
+    f32v2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32v2 v2_mul(f32v2 a, f32v2 b) {
+    f32v2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32v2 v2_fma(f32v2 a, f32v2 b, f32v2 c) {
+    f32v2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f32v2 v2_neg(f32v2 a) { return a ^ 0x8000000080000000ull; }
+
+// s += a * b in both lanes (fma_acc)
+__device__ __forceinline__ void fma_acc_v2(const f32x2v2 &a, const f32x2v2 &b, f32x2v2 &s) {
+    const f32v2 ph = v2_mul(a.hi, b.hi);
+    f32v2 pl = v2_fma(a.hi, b.hi, v2_neg(ph));
+    pl = v2_fma(a.hi, b.lo, pl);
+    pl = v2_fma(a.lo, b.hi, pl);
+    const f32v2 t = v2_add(s.hi, ph);
+    const f32v2 bv = v2_sub(t, s.hi);
+    const f32v2 err = v2_add(v2_sub(s.hi, v2_sub(t, bv)), v2_sub(ph, bv));
+    s.lo = v2_add(s.lo, v2_add(err, pl));
+    s.hi = t;
+}
+
+// a - b renormalised, in both lanes (sub_pair)
+__device__ __forceinline__ f32x2v2 sub_pair_v2(const f32x2v2 &a, const f32x2v2 &b) {
+    const f32v2 t = v2_sub(a.hi, b.hi);
+    const f32v2 bv = v2_sub(t, a.hi);
+    const f32v2 err = v2_add(v2_sub(a.hi, v2_sub(t, bv)), v2_sub(v2_neg(b.hi), bv));
+    const f32v2 lo = v2_add(err, v2_sub(a.lo, b.lo));
+    f32x2v2 o;
+    o.hi = v2_add(t, lo);
+    o.lo = v2_sub(lo, v2_sub(o.hi, t));
+    return o;
+}
+
+// the two lanes' values hi + lo summed as doubles
+__device__ __forceinline__ double pair_v2_to_f64(const f32x2v2 &a) {
+    float h0, h1, l0, l1;
+    v2_unpack(a.hi, h0, h1);
+    v2_unpack(a.lo, l0, l1);
+    return (f2d_exact(h0) + f2d_exact(l0)) + (f2d_exact(h1) + f2d_exact(l1));
+}
+
 }  // namespace llg

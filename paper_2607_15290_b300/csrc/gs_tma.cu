@@ -63,14 +63,16 @@ __global__ void __launch_bounds__(NT, Ring<MAXV>::BLOCKS)
     extern __shared__ __align__(128) unsigned char smraw[];
     unsigned char *ring = smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u);
     __shared__ __align__(8) unsigned long long full[NS], empty[NS];
-    __shared__ f32x2 coef[MAXV];
+    __shared__ f32x2v2 coef[MAXV];   // the coefficient pair in both lanes
     __shared__ double red[NCW][MAXV];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int CH = lay.CH;
     const size_t SB = lay.stage_bytes(nv, MODE);
     if (tid < nv) {
         const double h = (MODE == PASS_UPD_DOT) ? gd->h1[tid] : ((MODE == PASS_UPD_NRM) ? gd->h2[tid] : 0.0);
-        coef[tid] = split_f64(h * gd->scale[tid]);
+        const f32x2 c = split_f64(h * gd->scale[tid]);
+        coef[tid].hi = v2_pack(c.hi, c.hi);
+        coef[tid].lo = v2_pack(c.lo, c.lo);
     }
     if (tid == 0) {
         for (int st = 0; st < NS; ++st) {
@@ -87,9 +89,9 @@ __global__ void __launch_bounds__(NT, Ring<MAXV>::BLOCKS)
     auto v0_s = [&](int st) { return reinterpret_cast<double *>(w_h_s(st) + (WLO ? 2 : 1) * CH); };
     auto vh_s = [&](int st, int i) { return reinterpret_cast<float *>(v0_s(st) + CH) + (size_t)2 * (i - 1) * CH; };
     bool failed = false;
-    f32x2 acc[MAXV];
+    f32x2v2 acc[MAXV];
 #pragma unroll
-    for (int i = 0; i < MAXV; ++i) acc[i] = f32x2{0.0f, 0.0f};
+    for (int i = 0; i < MAXV; ++i) acc[i] = f32x2v2{0ull, 0ull};
 
     if (warp == NCW) {
         // producer: lane 0 arms the stage's barrier, then the lanes share its copies
@@ -137,34 +139,48 @@ __global__ void __launch_bounds__(NT, Ring<MAXV>::BLOCKS)
             const int len = (int)std::min<long long>(CH, n - e0);
             const float *wh = w_h_s(st), *wl = w_l_s(st);
             const double *v0 = v0_s(st);
-            for (int r = tid; r < len; r += NC) {
-                const f32x2 w{wh[r], WLO ? wl[r] : 0.0f};
-                f32x2 v[MAXV];
-                v[0] = split_f64(v0[r]);
-#pragma unroll
-                for (int i = 1; i < MAXV; ++i)
-                    if (i < nv) {
-                        const float *b = vh_s(st, i);
-                        v[i] = f32x2{b[r], b[CH + r]};
-                    }
+            // two adjacent elements a thread, in the two lanes of packed registers (len is even);
+            // the basis values are read from the stage where they are used (no array of them
+            // held across the loops)
+            for (int r = 2 * tid; r < len; r += 2 * NC) {
+                f32x2v2 w;
+                w.hi = *reinterpret_cast<const f32v2 *>(wh + r);
+                w.lo = WLO ? *reinterpret_cast<const f32v2 *>(wl + r) : 0ull;
+                f32x2v2 v0p;
+                {
+                    const double2 d = *reinterpret_cast<const double2 *>(v0 + r);
+                    const f32x2 s0 = split_f64(d.x), s1 = split_f64(d.y);
+                    v0p.hi = v2_pack(s0.hi, s1.hi);
+                    v0p.lo = v2_pack(s0.lo, s1.lo);
+                }
+                auto vload = [&](int i) {
+                    const float *b = vh_s(st, i);
+                    f32x2v2 q;
+                    q.hi = *reinterpret_cast<const f32v2 *>(b + r);
+                    q.lo = *reinterpret_cast<const f32v2 *>(b + CH + r);
+                    return q;
+                };
                 if (MODE == PASS_DOT) {
+                    fma_acc_v2(v0p, w, acc[0]);
 #pragma unroll
-                    for (int i = 0; i < MAXV; ++i)
-                        if (i < nv) fma_acc(v[i], w, acc[i]);
+                    for (int i = 1; i < MAXV; ++i)
+                        if (i < nv) fma_acc_v2(vload(i), w, acc[i]);
                 } else {
-                    f32x2 u{0.0f, 0.0f};
+                    f32x2v2 u{0ull, 0ull};
+                    fma_acc_v2(coef[0], v0p, u);
 #pragma unroll
-                    for (int i = 0; i < MAXV; ++i)
-                        if (i < nv) fma_acc(coef[i], v[i], u);
-                    const f32x2 wn = sub_pair(w, u);
-                    o_hi[e0 + r] = wn.hi;
-                    o_lo[e0 + r] = wn.lo;
+                    for (int i = 1; i < MAXV; ++i)
+                        if (i < nv) fma_acc_v2(coef[i], vload(i), u);
+                    const f32x2v2 wn = sub_pair_v2(w, u);
+                    *reinterpret_cast<f32v2 *>(o_hi + e0 + r) = wn.hi;
+                    *reinterpret_cast<f32v2 *>(o_lo + e0 + r) = wn.lo;
                     if (MODE == PASS_UPD_DOT) {
+                        fma_acc_v2(v0p, wn, acc[0]);
 #pragma unroll
-                        for (int i = 0; i < MAXV; ++i)
-                            if (i < nv) fma_acc(v[i], wn, acc[i]);
+                        for (int i = 1; i < MAXV; ++i)
+                            if (i < nv) fma_acc_v2(vload(i), wn, acc[i]);
                     } else {
-                        fma_acc(wn, wn, acc[0]);
+                        fma_acc_v2(wn, wn, acc[0]);
                     }
                 }
             }
@@ -182,7 +198,7 @@ __global__ void __launch_bounds__(NT, Ring<MAXV>::BLOCKS)
 #pragma unroll
         for (int i = 0; i < MAXV; ++i) {
             if (i < nout) {
-                double v = failed ? 0.0 : pair_to_f64(acc[i]);
+                double v = failed ? 0.0 : pair_v2_to_f64(acc[i]);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
                 if (lane == 0) red[warp][i] = v;
