@@ -674,7 +674,13 @@ def apply_sweep(args):
         ctx = L.Context(n)
         ctx.set_pass_plan(L.PLAN_CLUSTER if args.pass_plan == "cluster" else L.PLAN_FIVE)
         f32 = args.precision == "fp32"
-        tuning = "" if args.no_autotune else ctx.autotune(fp64=not f32, fp32=f32)
+        if args.axis_shapes:
+            for item in args.axis_shapes.split(";"):
+                slot, shape = item.split("=")
+                ctx.set_axis_shape(slot.strip(), shape.strip())
+            tuning = "fixed FP32 shapes: " + args.axis_shapes
+        else:
+            tuning = "" if args.no_autotune else ctx.autotune(fp64=not f32, fp32=f32)
         dt = torch.float32 if f32 else torch.float64
         m = torch.tensor(I.smooth3d(n) if len(n) == 3 else I.smooth2d(n), device="cuda").to(dt)
         p = torch.randn((4,) + tuple(reversed(n)), device="cuda", dtype=dt)

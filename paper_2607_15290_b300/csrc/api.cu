@@ -145,20 +145,38 @@ __global__ void k_min_norm2(const double *__restrict__ m, long long N, double *p
     double v = -1e300;
     for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
         const double a = m[j], b = m[N + j], c = m[2 * N + j];
-        v = fmax(v, -(a * a + b * b + c * c));
+        const double q = -(a * a + b * b + c * c);
+        v = q != q ? 1e308 : fmax(v, q);   // a non-finite node fails the check too
     }
     block_max_store(v, partials + (long long)blockIdx.x * RB_STRIDE);
 }
 
+// max over the blocks' partials, the whole block reading them (launch with RB_THREADS)
 __global__ void k_max_partials(const double *__restrict__ partials, int nb, double *dst) {
-    if (threadIdx.x != 0) return;
     double s = -1e300;
-    for (int b = 0; b < nb; ++b) s = fmax(s, partials[(long long)b * RB_STRIDE]);
-    *dst = s;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s = fmax(s, partials[(long long)b * RB_STRIDE]);
+    block_max_store(s, dst);
 }
 
 __global__ void k_sum_partials_n(const double *__restrict__ partials, int nb, int cnt, double *dst) {
     block_sum_partials(partials, nb, cnt, dst);
+}
+
+// the FP32 copy of the nodal field m (3 planes) and, in the same pass, per-block maxima of
+// -|m_i|^2 (the degenerate-node check of flexible solves)
+__global__ void k_to_f32_minnorm(const double *__restrict__ m, float *__restrict__ m32, long long N, double *partials) {
+    long long lo, hi;
+    block_chunk(N, lo, hi);
+    double v = -1e300;
+    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+        const double a = m[j], b = m[N + j], c = m[2 * N + j];
+        m32[j] = d2f_rn(a);
+        m32[N + j] = d2f_rn(b);
+        m32[2 * N + j] = d2f_rn(c);
+        const double q = -(a * a + b * b + c * c);
+        v = q != q ? 1e308 : fmax(v, q);   // a non-finite node fails the check too
+    }
+    block_max_store(v, partials + (long long)blockIdx.x * RB_STRIDE);
 }
 
 __global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, long long n) {
@@ -201,9 +219,14 @@ __global__ void k_axpy3(const double *__restrict__ m, const double *__restrict__
 
 // Picard advance: mhat' = m + hk v, and the exact residual of x for the new blocks,
 // r0 = r_prev - [A(mhat') - A(mhat)] x = r_prev - (dm x v + dm r, -dm . v), dm = mhat' - mhat
-// (only the nodal skew/constraint blocks depend on the midpoint field)
-__global__ void k_picard_advance(const double *__restrict__ m, const double *__restrict__ x, double hk, double *mhat,
-                                 const double *__restrict__ rprev, double *r0, long long N) {
+// (only the nodal skew/constraint blocks depend on the midpoint field), written over r_prev,
+// with per-block partial sums of |r0|^2
+__global__ void __launch_bounds__(RB_THREADS) k_picard_advance(const double *__restrict__ m, const double *__restrict__ x,
+                                                               double hk, double *mhat, double *r, long long N,
+                                                               double *partials) {
+    const double *rprev = r;
+    double *r0 = r;
+    double acc[1] = {0.0};
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
         const double v1 = x[j], v2 = x[N + j], v3 = x[2 * N + j], r = x[3 * N + j];
         const double a1 = m[j] + hk * v1, a2 = m[N + j] + hk * v2, a3 = m[2 * N + j] + hk * v3;
@@ -215,21 +238,31 @@ __global__ void k_picard_advance(const double *__restrict__ m, const double *__r
         mhat[j] = a1;
         mhat[N + j] = a2;
         mhat[2 * N + j] = a3;
+        acc[0] += r0[j] * r0[j] + r0[N + j] * r0[N + j] + r0[2 * N + j] * r0[2 * N + j] + r0[3 * N + j] * r0[3 * N + j];
     }
+    block_reduce_store<1>(acc, 1, partials + (long long)blockIdx.x * RB_STRIDE);
 }
 
-// partial sums of |v - vold|^2 and |v|^2
-__global__ void k_picard_norms(const double *__restrict__ v, const double *__restrict__ vold, long long n3, double *partials) {
+// partial sums of |v - vold|^2 and |v|^2 for the Picard stopping test, then vold = v.  The
+// difference is formed in FP64; the squares are summed in FP32 per thread (the test compares
+// the two norms to a tolerance: six significant digits are plenty) and in FP64 across
+// threads, off the FP64 unit that the three multiply-adds a value would otherwise load.
+__global__ void __launch_bounds__(RB_THREADS) k_picard_norms_advance(const double *__restrict__ v, double *__restrict__ vold,
+                                                                     long long n3, double *partials) {
     long long lo, hi;
     block_chunk(n3, lo, hi);
-    double acc[2] = {0.0, 0.0};
+    float s0 = 0.0f, s1 = 0.0f;
     for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-        const double d = v[e] - vold[e];
-        acc[0] += d * d;
-        acc[1] += v[e] * v[e];
+        const double ve = v[e];
+        const float d = d2f_rn(ve - vold[e]), vf = d2f_rn(ve);
+        s0 = __fmaf_rn(d, d, s0);
+        s1 = __fmaf_rn(vf, vf, s1);
+        vold[e] = ve;
     }
+    double acc[2] = {(double)s0, (double)s1};
     block_reduce_store<2>(acc, 2, partials + (long long)blockIdx.x * RB_STRIDE);
 }
+
 
 // m^{n+1} = m^n + k v and max_i | |m^{n+1}_i| - |m^n_i| |
 __global__ void k_mid_final(const double *__restrict__ m, const double *__restrict__ v, double k, double *mn,
@@ -465,7 +498,7 @@ llg_status op_scaled_copy(llg_ctx *c, const TI *x, const double *scale, TO *y) {
 llg_status check_nodes(llg_ctx *c, const double *m) {
     const int nb = reduction_blocks(c);
     k_min_norm2<<<nb, RB_THREADS, 0, c->stream>>>(m, c->geo.N, c->red);
-    k_max_partials<<<1, 32, 0, c->stream>>>(c->red, nb, c->dsc);
+    k_max_partials<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, c->dsc);
     c->launches += 2;
     llg_status st = cuda_check(c, cudaGetLastError(), "node check");
     if (st != LLG_OK) return st;
@@ -477,13 +510,20 @@ llg_status check_nodes(llg_ctx *c, const double *m) {
 }
 
 // solve A(m; theta) x = b with the chosen precision
+// r0_ready: r0 is the workspace's own first-residual buffer with its squared norm already
+// queued into device scalar 2 (the midpoint step's in-place Picard advance)
+// bnorm_slot >= 0: ||b||^2 is already queued into that device scalar
 llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *o, const double *m, const double *b,
-                 double *x, llg_info *info, const double *r0 = nullptr) {
-    llg_status st = check_nodes(c, m);
-    if (st != LLG_OK) return st;
+                 double *x, llg_info *info, const double *r0 = nullptr, bool r0_ready = false, int bnorm_slot = -1) {
     const bool flex = o->precision == LLG_PREC_FP32_FLEX;
+    llg_status st = LLG_OK;
+    // FP64 solves check the nodes here; flexible solves in the pass that makes the FP32 copy
+    // of m, read with the solve's first device scalars (no host round trip of its own)
+    if (!flex && (st = check_nodes(c, m)) != LLG_OK) return st;
     if ((st = ensure_spec(c, true, flex)) != LLG_OK) return st;
     SolveOps ops;
+    ops.r0_ready = r0_ready;
+    ops.bnorm_slot = bnorm_slot;
     // the true residuals: FP64 chain, or the FP32-pair chain where every axis has one
     if (o->chain_arith == LLG_CHAIN_F32X2 && pair_chains_available(c))
         ops.matvec = [=](const double *xx, double *yy) { return op_matvec_pair(c, p, theta, m, xx, yy); };
@@ -507,8 +547,12 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
         }
     } else {
         if ((st = ensure_m32(c)) != LLG_OK) return st;
-        k_to_f32<<<grid_blocks(c), RB_THREADS, 0, c->stream>>>(m, c->m32, 3 * c->geo.N);
-        c->launches++;
+        const int nb = reduction_blocks(c);
+        k_to_f32_minnorm<<<nb, RB_THREADS, 0, c->stream>>>(m, c->m32, c->geo.N, c->red);
+        k_max_partials<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, c->dsc + SolveOps::NODE_CHECK_SLOT);
+        c->launches += 2;
+        if ((st = cuda_check(c, cudaGetLastError(), "FP32 field copy")) != LLG_OK) return st;
+        ops.node_check = true;
         const float *m32 = c->m32;
         ops.fprec = [=](const double *xx, const double *s, float *zz) {
             if (pc == LLG_PC_NONE) return op_scaled_copy<float>(c, xx, s, zz);
@@ -535,6 +579,26 @@ llg_status solve(llg_ctx *c, const llg_params *p, double theta, const llg_opts *
             io.skip = cyc;
             return spectral_chain<float, float, float>(c, IN_V, OUT_MATVEC, io, sym_forward(c, p, theta));
         };
+        if (pc != LLG_PC_NONE && chain_pm_available(c)) {
+            // preconditioner and matvec in one sequence: the x-pass inverse of the first fused
+            // with the x-pass forward of the second
+            ops.fpm = [=](const double *xx, const double *s, float *zz, float *ww) {
+                auto io1 = make_io<double, float, float>(m32, xx, zz, s, p->lambda);
+                io1.plain_nodal = pc == LLG_PC_HERMITIAN;
+                io1.skip = cyc;
+                auto io2 = make_io<float, float, float>(m32, zz, ww, nullptr, p->lambda);
+                io2.skip = cyc;
+                return spectral_chain_pm<double>(c, io1, sym_shifted_inverse(c, p, theta), io2, sym_forward(c, p, theta));
+            };
+            ops.fpm32 = [=](const float *xx, const double *s, float *zz, float *ww) {
+                auto io1 = make_io<float, float, float>(m32, xx, zz, s, p->lambda);
+                io1.plain_nodal = pc == LLG_PC_HERMITIAN;
+                io1.skip = cyc;
+                auto io2 = make_io<float, float, float>(m32, zz, ww, nullptr, p->lambda);
+                io2.skip = cyc;
+                return spectral_chain_pm<float>(c, io1, sym_shifted_inverse(c, p, theta), io2, sym_forward(c, p, theta));
+            };
+        }
     }
     return gmres_run(c, ops, flex, o, b, x, info, r0);
 }
@@ -1011,7 +1075,7 @@ llg_status llg_step_euler(llg_ctx *c, const llg_params *p, const llg_opts *o, co
     llg_status solve_st = st;
     const int nb = reduction_blocks(c);
     k_euler_update<<<nb, RB_THREADS, 0, c->stream>>>(m_n, x_out, p->k, m_next, N, c->red);
-    k_max_partials<<<1, 32, 0, c->stream>>>(c->red, nb, c->dsc + 9);
+    k_max_partials<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, c->dsc + 9);
     c->launches += 2;
     if ((st = cuda_check(c, cudaGetLastError(), "euler update")) != LLG_OK) return st;
     if (o->diagnostics) {
@@ -1028,6 +1092,9 @@ llg_status llg_step_euler(llg_ctx *c, const llg_params *p, const llg_opts *o, co
     if (info) *info = inf;
     return solve_st;
 }
+
+// device scalar that holds ||b||^2 across the solves of a midpoint step
+constexpr int kBnormSlot = 4;
 
 llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o, const double *m_n, const double *v_prev,
                              double *m_next, double *x_out, llg_info *info) {
@@ -1056,6 +1123,8 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
     k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, v_prev, 0.5 * p->k, mhat, 3 * N);
     if ((st = lowfield_nodal(c, p, mhat, hfbuf, &hf)) != LLG_OK) return st;
     if ((st = rhs_velocity(c, p, o, m_n, hf, b)) != LLG_OK) return st;
+    // ||b||^2 once for the step's solves (device scalar kBnormSlot)
+    if ((st = dot_async(c, b, b, 4 * N, c->dsc + kBnormSlot)) != LLG_OK) return st;
     // warm start (v_prev | 0), or zero
     if (v_prev) cudaMemcpyAsync(x_out, v_prev, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
     else cudaMemsetAsync(x_out, 0, sizeof(double) * 3 * N, c->stream);
@@ -1066,7 +1135,7 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
     bool have_r0 = false;
     for (int it = 0; it < o->picard_max; ++it) {
         llg_info si = llg_info();
-        st = solve(c, p, 0.5, o, mhat, b, x_out, &si, have_r0 ? r0 : nullptr);
+        st = solve(c, p, 0.5, o, mhat, b, x_out, &si, have_r0 ? r0 : nullptr, have_r0, kBnormSlot);
         inf.iters += si.iters;
         inf.restarts += si.restarts;
         inf.applies += si.applies;
@@ -1075,24 +1144,33 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
         if (st == LLG_ERR_NOT_CONVERGED) lin_st = st;
         else if (st != LLG_OK) { inf.status = st; if (info) *info = inf; return st; }
         if (it >= 1) {
-            k_picard_norms<<<nb, RB_THREADS, 0, c->stream>>>(x_out, vold, 3 * N, c->red);
+            // the stopping test's norms, and vold = v in the same pass
+            k_picard_norms_advance<<<nb, RB_THREADS, 0, c->stream>>>(x_out, vold, 3 * N, c->red);
             k_sum_partials_n<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, 2, c->dsc);
             c->launches += 2;
             if ((st = sync_scalars(c, 2)) != LLG_OK) return st;
             if (std::sqrt(c->hsc[0]) <= o->picard_tol * std::sqrt(c->hsc[1])) { conv = true; break; }
+        } else {
+            cudaMemcpyAsync(vold, x_out, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
         }
-        cudaMemcpyAsync(vold, x_out, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
         if (mdep) {
             // the right-hand side moves with mhat: rebuild it, solve from the true residual
             k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, 3 * N);
             c->launches++;
             if ((st = lowfield_nodal(c, p, mhat, hfbuf, &hf)) != LLG_OK) return st;
             if ((st = rhs_velocity(c, p, o, m_n, hf, b)) != LLG_OK) return st;
+            if ((st = dot_async(c, b, b, 4 * N, c->dsc + kBnormSlot)) != LLG_OK) return st;
             have_r0 = false;
             continue;
         }
         if (c->ws.last_res) {
-            k_picard_advance<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, c->ws.last_res, r0, N);
+            // the last solve's final true residual, advanced in place (it is the next solve's
+            // first residual and first basis vector), its squared norm into device scalar 2
+            double *res = const_cast<double *>(c->ws.last_res);
+            k_picard_advance<<<nb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, res, N, c->red);
+            k_sum_partials_n<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, 1, c->dsc + 2);
+            c->launches++;
+            r0 = res;
             have_r0 = true;
         } else {
             k_axpy3<<<gb, RB_THREADS, 0, c->stream>>>(m_n, x_out, 0.5 * p->k, mhat, 3 * N);
@@ -1101,7 +1179,7 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
         c->launches++;
     }
     k_mid_final<<<nb, RB_THREADS, 0, c->stream>>>(m_n, x_out, p->k, m_next, N, c->red);
-    k_max_partials<<<1, 32, 0, c->stream>>>(c->red, nb, c->dsc + 9);
+    k_max_partials<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, c->dsc + 9);
     c->launches += 2;
     if ((st = cuda_check(c, cudaGetLastError(), "midpoint update")) != LLG_OK) return st;
     if (o->diagnostics) {

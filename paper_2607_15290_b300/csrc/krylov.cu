@@ -622,15 +622,23 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
 
     // ||b||^2 -> dsc[0]; with a caller's initial residual r0 (copied into V_0 or T), ||r0||^2
     // -> dsc[2] in the same round trip
-    if ((st = dot_async(c, b, b, n, dsc)) != LLG_OK) return st;
+    if (ops.bnorm_slot < 0 && (st = dot_async(c, b, b, n, dsc)) != LLG_OK) return st;
     if (r0) {
         double *dst = flexible ? w.V : w.T;
-        cudaError_t ce = cudaMemcpyAsync(dst, r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
-        if ((st = cuda_check(c, ce, "initial residual")) != LLG_OK) return st;
-        if ((st = dot_async(c, dst, dst, n, dsc + 2)) != LLG_OK) return st;
+        if (!(ops.r0_ready && dst == r0)) {
+            cudaError_t ce = cudaMemcpyAsync(dst, r0, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+            if ((st = cuda_check(c, ce, "initial residual")) != LLG_OK) return st;
+            if ((st = dot_async(c, dst, dst, n, dsc + 2)) != LLG_OK) return st;
+        }
     }
-    if ((st = sync_read(c, hsc, dsc, (r0 ? 3 : 1) * sizeof(double))) != LLG_OK) return st;
-    const double nb = std::sqrt(hsc[0]);
+    const int nread = std::max(std::max(ops.node_check ? SolveOps::NODE_CHECK_SLOT + 1 : 1, r0 ? 3 : 1), ops.bnorm_slot + 1);
+    if ((st = sync_read(c, hsc, dsc, nread * sizeof(double))) != LLG_OK) return st;
+    if (ops.node_check) {
+        const double minn2 = -hsc[SolveOps::NODE_CHECK_SLOT];
+        if (!(minn2 > 0.0) || !std::isfinite(minn2))
+            return set_error(c, LLG_ERR_DEGENERATE_NODE, "some node has |m_i| = 0 (or non-finite): the saddle matrix is singular");
+    }
+    const double nb = std::sqrt(hsc[ops.bnorm_slot < 0 ? 0 : ops.bnorm_slot]);
     llg_info inf = llg_info();
     if (nb == 0.0) {
         cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream);
@@ -683,9 +691,15 @@ llg_status gmres_run(llg_ctx *c, const SolveOps &ops, bool flexible, const llg_o
                 st = ops.pop(vj, scale_j, w.W);
             } else if (pairs) {
                 float *zj = w.Z + (long long)j * n;
+                float *w32 = reinterpret_cast<float *>(w.W);
                 // V_0 is FP64; V_j (j >= 1) a planar pair whose hi plane the FP32 preconditioner reads
-                st = j == 0 ? ops.fprec(vj, scale_j, zj) : ops.fprec32(reinterpret_cast<const float *>(vj), scale_j, zj);
-                if (st == LLG_OK) st = ops.fmatvec32(zj, reinterpret_cast<float *>(w.W));
+                if (ops.fpm && ops.fpm32) {
+                    st = j == 0 ? ops.fpm(vj, scale_j, zj, w32)
+                                : ops.fpm32(reinterpret_cast<const float *>(vj), scale_j, zj, w32);
+                } else {
+                    st = j == 0 ? ops.fprec(vj, scale_j, zj) : ops.fprec32(reinterpret_cast<const float *>(vj), scale_j, zj);
+                    if (st == LLG_OK) st = ops.fmatvec32(zj, w32);
+                }
             } else {
                 float *zj = w.Z + (long long)j * n;
                 st = ops.fprec(vj, scale_j, zj);

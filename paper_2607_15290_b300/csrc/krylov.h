@@ -45,6 +45,21 @@ struct SolveOps {
     // of a planar-pair basis vector), and w = A z stored FP32 (the hi plane of w)
     std::function<llg_status(const float *x, const double *scale, float *z)> fprec32;
     std::function<llg_status(const float *z, float *w)> fmatvec32;
+    // the same two operators as one fused sequence (z written, then w = A z), from the FP64
+    // first basis vector or from the hi plane of a later one; empty when unavailable
+    std::function<llg_status(const double *x, const double *scale, float *z, float *w)> fpm;
+    std::function<llg_status(const float *x, const double *scale, float *z, float *w)> fpm32;
+    // the caller has queued max_i -|m_i|^2 into device scalar NODE_CHECK_SLOT: gmres_run reads
+    // it with its first scalars and fails with LLG_ERR_DEGENERATE_NODE unless |m_i| > 0
+    static constexpr int NODE_CHECK_SLOT = 3;
+    bool node_check = false;
+    // the initial residual passed to gmres_run already sits in the workspace buffer the
+    // cycle starts from (V_0, or T for left preconditioning) and its squared norm in device
+    // scalar 2: no copy, no dot product
+    bool r0_ready = false;
+    // >= 0: ||b||^2 already sits in this device scalar (the right-hand side is shared by the
+    // solves of a step): no dot product
+    int bnorm_slot = -1;
 };
 
 llg_status ensure_workspace(llg_ctx *c, int restart, bool flexible);

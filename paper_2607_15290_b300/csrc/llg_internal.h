@@ -213,6 +213,12 @@ llg_status anisotropy_add(llg_ctx *c, const double *m, double kan, const double 
 template <typename T, typename TIn, typename TOut>
 llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<TIn, TOut, T> &io,
                           const Symbol &sym);
+// z = M^{-1} (s v) (IN_V, OUT_APPLY) then w = A z (IN_V unscaled, OUT_MATVEC), FP32, the first
+// chain's x-pass inverse fused with the second's x-pass forward (nine passes, z still written)
+bool chain_pm_available(const llg_ctx *c);
+template <typename TIn1>
+llg_status spectral_chain_pm(llg_ctx *c, const NodalIO<TIn1, float, float> &io1, const Symbol &sym1,
+                             const NodalIO<float, float, float> &io2, const Symbol &sym2);
 
 // reductions.cu / krylov.cu
 int reduction_blocks(llg_ctx *c);

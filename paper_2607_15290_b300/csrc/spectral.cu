@@ -361,6 +361,95 @@ llg_status spectral_chain(llg_ctx *c, int in_mode, int out_mode, const NodalIO<T
     return LLG_OK;
 }
 
+// the axis passes between the x passes of a five-pass (3D) or three-pass (2D) FP32 round trip
+static llg_status axis_passes32(llg_ctx *c, const Symbol &sym, const int *skip) {
+    const SpecGeom &g = c->geo;
+    const int n0 = g.n[0];
+    const double CB = 2.0 * sizeof(float), livec = (double)(n0 + n0 / 2 + 1), live = (double)g.rows * livec;
+    auto fftf = [](double lines, int n, int logn) { return lines * 5.0 * n * logn; };
+    auto run_slot = [&](int slot, double flops) -> cudaError_t {
+        ColArgs<float> ca{};
+        int batches = 1, mode = 7;
+        slot_args<float>(c, slot, sym, ca, batches, mode);
+        ca.skip = skip;
+        prof_begin(c, K_AXIS, 2 * live * CB, flops);
+        cudaError_t err = launch_col_cfg<float>(c, mode, ca, batches, slot_cfg<float>(c, slot, ca.nl));
+        prof_end(c);
+        c->launches++;
+        return err;
+    };
+    cudaError_t e;
+    if (g.dim == 2) {
+        if ((e = run_slot(SLOT_2D, 2 * fftf(livec, g.n[1], g.logn[1]))) != cudaSuccess) return cuda_check(c, e, "y-pass");
+        return LLG_OK;
+    }
+    const double ylines = livec * g.n[2], zlines = livec * g.n[1];
+    if ((e = run_slot(SLOT_Y_FWD, fftf(ylines, g.n[1], g.logn[1]))) != cudaSuccess) return cuda_check(c, e, "y-pass forward");
+    if ((e = run_slot(SLOT_Z, 2 * fftf(zlines, g.n[2], g.logn[2]))) != cudaSuccess) return cuda_check(c, e, "z-pass");
+    if ((e = run_slot(SLOT_Y_INV, fftf(ylines, g.n[1], g.logn[1]))) != cudaSuccess) return cuda_check(c, e, "y-pass inverse");
+    return LLG_OK;
+}
+
+bool chain_pm_available(const llg_ctx *c) {
+    return c->pass_plan == LLG_PLAN_FIVE && ct::covers(c->geo.logn[0]) && c->spec32 != nullptr;
+}
+
+template <typename TIn1>
+llg_status spectral_chain_pm(llg_ctx *c, const NodalIO<TIn1, float, float> &io1, const Symbol &sym1,
+                             const NodalIO<float, float, float> &io2, const Symbol &sym2) {
+    const SpecGeom &g = c->geo;
+    const int n0 = g.n[0];
+    if (!chain_pm_available(c) || io2.scale != nullptr || io1.skip != io2.skip)
+        return set_error(c, LLG_ERR_INVALID_ARG, "fused preconditioner-matvec chain: unsupported arguments");
+    const int E = row_E<float>(n0), P = n0 / E;
+    const long long pairs = g.rows / 2;
+    int G = 256 / (3 * P);
+    if (G < 1) G = 1;
+    long long want = pairs / (2LL * c->sm_count);
+    if (want < G) G = (int)(want < 1 ? 1 : want);
+    const int blocks = (int)((pairs + G - 1) / G);
+    const int threads = 3 * G * P;
+    const size_t smr = ct::row_smem<float>(n0, G);
+    RowArgs<float, TIn1, float> ra1;
+    ra1.spec = spec_of<float>(c);
+    ra1.tw0 = tw_of<float>(c, 0);
+    ra1.n0 = n0; ra1.logn0 = g.logn[0]; ra1.S = g.S; ra1.G = G;
+    ra1.rows = g.rows; ra1.N = g.N; ra1.io = io1;
+    RowArgs<float, float, float> ra2;
+    ra2.spec = ra1.spec; ra2.tw0 = ra1.tw0;
+    ra2.n0 = n0; ra2.logn0 = g.logn[0]; ra2.S = g.S; ra2.G = G;
+    ra2.rows = g.rows; ra2.N = g.N; ra2.io = io2;
+    const double W = 4.0, CB = 8.0, Nd = (double)g.N, live = (double)g.rows * (n0 + n0 / 2 + 1);
+    const double xf = (double)g.rows * 1.5 * 5.0 * n0 * g.logn[0];
+    cudaError_t e;
+    llg_status st;
+    prof_begin(c, K_XFWD, 3 * Nd * sizeof(TIn1) + live * CB, xf);
+    e = ct::row_fwd<float, TIn1, float>(c, g.logn[0], IN_V, ra1, blocks, threads, smr);
+    prof_end(c);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_check(c, e, "x-pass forward");
+    if ((st = axis_passes32(c, sym1, io1.skip)) != LLG_OK) return st;
+    // x-pass inverse of the preconditioner (reads the spectrum, m, r; writes z) and x-pass
+    // forward of the matvec from z in shared memory (writes the spectrum)
+    prof_begin(c, K_XINV, 2 * live * CB + Nd * (3 * W + sizeof(TIn1) + 4 * W), 2 * xf);
+    e = ct::row_inv_fwd<TIn1>(c, g.logn[0], ra1, ra2, blocks, threads, smr);
+    prof_end(c);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_check(c, e, "x-pass inverse + forward");
+    if ((st = axis_passes32(c, sym2, io2.skip)) != LLG_OK) return st;
+    prof_begin(c, K_XINV, live * CB + Nd * (3 * W + 4 * W + 4 * W), xf);
+    e = ct::row_inv<float, float, float>(c, g.logn[0], OUT_MATVEC, ra2, blocks, threads, smr);
+    prof_end(c);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_check(c, e, "x-pass inverse");
+    return LLG_OK;
+}
+
+template llg_status spectral_chain_pm<double>(llg_ctx *, const NodalIO<double, float, float> &, const Symbol &,
+                                              const NodalIO<float, float, float> &, const Symbol &);
+template llg_status spectral_chain_pm<float>(llg_ctx *, const NodalIO<float, float, float> &, const Symbol &,
+                                             const NodalIO<float, float, float> &, const Symbol &);
+
 llg_status plain_axis_pass64(llg_ctx *c, int axis, bool forward) {
     if (axis != 1 || c->geo.dim != 3) return set_error(c, LLG_ERR_INVALID_ARG, "plain axis pass: 3D y axis only");
     ColArgs<double> ca{};

@@ -32,25 +32,22 @@ template <typename C> struct SpecSink {
     __device__ __forceinline__ void operator()(long long row, int col, C v) const { base[row * S + col] = v; }
 };
 
-template <typename T, typename TIn, typename TOut, int LOGN, int IN, class Sink>
-__device__ __forceinline__ void row_fwd_ct_body_to(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw,
-                                                   const Sink &sink) {
+// prologue of the forward x pass: node-parallel, unit-stride plane loads (KC nodes per
+// thread in flight), transformed nodal values staged into buf1 with layout 0
+template <typename T, typename TIn, typename TOut, int LOGN, int IN>
+__device__ __forceinline__ void row_fwd_stage(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw) {
     using C = cplx<T>;
     using L = RowL<LOGN>;
     constexpr int N = 1 << LOGN, E = LineE<T, LOGN>::value, P = N / E, LS = L::size;
-    constexpr int LOGP = LOGN - (E == 16 ? 4 : 3);
     const int G = a.G;
     // one line of LS per P threads: 3 G lines carry data; a block larger than 3 G P (the
     // ensemble's) transforms its spare lines without storing them
     C *buf0 = reinterpret_cast<C *>(smraw);
     C *buf1 = buf0 + (blockDim.x / P) * LS;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const long long Nn = a.N, npairs = a.rows / 2, pair0 = bidx * G;
+    const long long Nn = a.N, pair0 = bidx * G;
     const NodalIO<TIn, TOut, T> &io = a.io;
     const T s = in_scale(io);
-
-    // prologue: node-parallel, unit-stride plane loads (KC nodes per thread in
-    // flight), transformed nodal values staged into buf1 with layout 0
     constexpr int KC = sizeof(T) == 4 ? 6 : 3;
     constexpr bool NEED_M = InShape<IN>::NEED_M;
     constexpr int NX = InShape<IN>::NX;
@@ -105,8 +102,22 @@ __device__ __forceinline__ void row_fwd_ct_body_to(const RowArgs<T, TIn, TOut> &
             reinterpret_cast<T *>(&buf1[(3 * gp + 2) * LS + e])[rr] = u3;
         }
     }
-    __syncthreads();
+}
 
+// the rest of the forward x pass, from the rows staged in buf1: packed transforms, half
+// spectra, every spectral value handed to the sink
+template <typename T, typename TIn, typename TOut, int LOGN, class Sink>
+__device__ __forceinline__ void row_fwd_transform(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw,
+                                                  const Sink &sink) {
+    using C = cplx<T>;
+    using L = RowL<LOGN>;
+    constexpr int N = 1 << LOGN, E = LineE<T, LOGN>::value, P = N / E, LS = L::size;
+    constexpr int LOGP = LOGN - (E == 16 ? 4 : 3);
+    const int G = a.G;
+    C *buf0 = reinterpret_cast<C *>(smraw);
+    C *buf1 = buf0 + (blockDim.x / P) * LS;
+    const int tid = threadIdx.x;
+    const long long npairs = a.rows / 2, pair0 = bidx * G;
     const int line = tid >> LOGP, t = tid & (P - 1);
     const int gp = line / 3, kind = line - 3 * gp;
     const long long pair = pair0 + gp;
@@ -145,6 +156,14 @@ __device__ __forceinline__ void row_fwd_ct_body_to(const RowArgs<T, TIn, TOut> &
     }
 }
 
+template <typename T, typename TIn, typename TOut, int LOGN, int IN, class Sink>
+__device__ __forceinline__ void row_fwd_ct_body_to(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw,
+                                                   const Sink &sink) {
+    row_fwd_stage<T, TIn, TOut, LOGN, IN>(a, bidx, smraw);
+    __syncthreads();
+    row_fwd_transform<T, TIn, TOut, LOGN>(a, bidx, smraw, sink);
+}
+
 template <typename T, typename TIn, typename TOut, int LOGN, int IN>
 __device__ __forceinline__ void row_fwd_ct_body(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw) {
     row_fwd_ct_body_to<T, TIn, TOut, LOGN, IN>(a, bidx, smraw, SpecSink<cplx<T>>{a.spec, (long long)a.S});
@@ -162,9 +181,13 @@ __global__ void __launch_bounds__(512) row_fwd_ct(RowArgs<T, TIn, TOut> a) {
 
 // With `in` set, the spectrum of pair p is read from rows 2 (p - in_pair0) (+1) of `in`
 // (row stride in_S) instead of the global spectrum.
-template <typename T, typename TIn, typename TOut, int LOGN, int OUT>
+// STAGE_FWD (OUT_APPLY only): the velocity part of every result is also staged into buf1 the
+// way row_fwd_stage stages an unscaled IN_V input, so that row_fwd_transform can transform it
+// next without reading it back
+template <typename T, typename TIn, typename TOut, int LOGN, int OUT, bool STAGE_FWD = false>
 __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, long long bidx, unsigned char *smraw,
                                                 const cplx<T> *in = nullptr, long long in_pair0 = 0, int in_S = 0) {
+    static_assert(!STAGE_FWD || OUT == OUT_APPLY, "staging follows the preconditioner's epilogue");
     using C = cplx<T>;
     using L = RowL<LOGN>;
     constexpr int N = 1 << LOGN, E = LineE<T, LOGN>::value, P = N / E, LS = L::size, HN = N / 2;
@@ -280,6 +303,12 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
                 if (!io.plain_nodal)
                     nodal_inverse<T, false>(mv[k][0], mv[k][1], mv[k][2], io.lam, w1, w2, w3, z4, z1, z2, z3, z4);
                 y[j] = cvt<TOut>(z1); y[Nn + j] = cvt<TOut>(z2); y[2 * Nn + j] = cvt<TOut>(z3); y[3 * Nn + j] = cvt<TOut>(z4);
+                if constexpr (STAGE_FWD) {
+                    // this node's slots of the staging layout (read above as fbase when fbase
+                    // is buf1: the same thread, read before written)
+                    buf1[(3 * gq + rr) * LS + e] = cmk<C>(cvt<T>(cvt<TOut>(z1)), cvt<T>(cvt<TOut>(z2)));
+                    reinterpret_cast<T *>(&buf1[(3 * gq + 2) * LS + e])[rr] = cvt<T>(cvt<TOut>(z3));
+                }
             } else if constexpr (OUT == OUT_FUSED) {
                 const T m1 = mv[k][0], m2 = mv[k][1], m3 = mv[k][2];
                 const T v1 = s * cvt<T>(xv[k][0]), v2 = s * cvt<T>(xv[k][1]), v3 = s * cvt<T>(xv[k][2]);
@@ -336,6 +365,19 @@ __global__ void __launch_bounds__(is_fpair<T>::value ? 384 : 512, is_fpair<T>::v
     if (a.io.skip && *a.io.skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     row_inv_ct_body<T, TIn, TOut, LOGN, OUT>(a, blockIdx.x, smraw);
+}
+
+// x-pass inverse of the preconditioner (OUT_APPLY, z written) fused with the x-pass forward of
+// the matvec that follows it on z (IN_V, unscaled): the forward reads z from shared memory.
+// Each block reads its own rows of the spectrum before it writes them, so one buffer serves.
+template <typename TIn1, int LOGN>
+__global__ void __launch_bounds__(512) row_inv_fwd_ct(RowArgs<float, TIn1, float> a1, RowArgs<float, float, float> a2) {
+    pdl_wait();
+    if (a1.io.skip && *a1.io.skip) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    row_inv_ct_body<float, TIn1, float, LOGN, OUT_APPLY, true>(a1, blockIdx.x, smraw);
+    __syncthreads();
+    row_fwd_transform<float, float, float, LOGN>(a2, blockIdx.x, smraw, SpecSink<float2>{a2.spec, (long long)a2.S});
 }
 
 // ------------------------------------------------------------------ axis passes

@@ -68,6 +68,15 @@ cudaError_t row_inv_launch(llg_ctx *c, int out_mode, const RowArgs<T, TIn, TOut>
     return cudaErrorInvalidValue;
 }
 
+template <typename TIn1, int LOGN>
+cudaError_t row_inv_fwd_launch(llg_ctx *c, const RowArgs<float, TIn1, float> &a1, const RowArgs<float, float, float> &a2,
+                               int blocks, int threads, size_t sm) {
+    auto k = row_inv_fwd_ct<TIn1, LOGN>;
+    cudaError_t e = prep(k);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k, dim3(blocks), dim3(threads), sm, c->stream, a1, a2);
+}
+
 template <typename T, int LOGN, int TW>
 static cudaError_t col_launch_tw(llg_ctx *c, int mode, const ColArgs<T> &a, dim3 grid) {
     constexpr int N = 1 << LOGN, E = LineE<T, LOGN>::value, threads = TW * (N / E);
@@ -179,6 +188,10 @@ LLG_CT_ROWS(float, float, double)
 LLG_CT_ROWS(float, float, float)
 LLG_CT_ROWS(fpair, double, double)
 #undef LLG_CT_ROWS
+template cudaError_t row_inv_fwd_launch<double, LLG_CT_LOGN>(llg_ctx *, const RowArgs<float, double, float> &,
+                                                             const RowArgs<float, float, float> &, int, int, size_t);
+template cudaError_t row_inv_fwd_launch<float, LLG_CT_LOGN>(llg_ctx *, const RowArgs<float, float, float> &,
+                                                            const RowArgs<float, float, float> &, int, int, size_t);
 template cudaError_t col_launch<double, LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<double> &, dim3, int);
 template cudaError_t col_launch<fpair, LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<fpair> &, dim3, int);
 template cudaError_t col_launch<float, LLG_CT_LOGN>(llg_ctx *, int, const ColArgs<float> &, dim3, int);

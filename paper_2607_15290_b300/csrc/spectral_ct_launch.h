@@ -16,6 +16,9 @@ template <typename T, typename TIn, typename TOut, int LOGN>
 cudaError_t row_inv_launch(llg_ctx *c, int out_mode, const RowArgs<T, TIn, TOut> &a, int blocks, int threads, size_t sm);
 template <typename T, int LOGN>
 cudaError_t col_launch(llg_ctx *c, int mode, const ColArgs<T> &a, dim3 grid, int TW);
+template <typename TIn1, int LOGN>
+cudaError_t row_inv_fwd_launch(llg_ctx *c, const RowArgs<float, TIn1, float> &a1, const RowArgs<float, float, float> &a2,
+                               int blocks, int threads, size_t sm);
 template <int LOGN>
 cudaError_t staged_launch(llg_ctx *c, int mode, const ColArgs<float> &a, int live, int batches, int TWL, int CB);
 template <int LOGN>
@@ -47,6 +50,11 @@ inline cudaError_t row_fwd(llg_ctx *c, int logn, int in_mode, const RowArgs<T, T
 template <typename T, typename TIn, typename TOut>
 inline cudaError_t row_inv(llg_ctx *c, int logn, int out_mode, const RowArgs<T, TIn, TOut> &a, int blocks, int threads, size_t sm) {
     LLG_CT_SWITCH(logn, (row_inv_launch<T, TIn, TOut, LG>(c, out_mode, a, blocks, threads, sm)))
+}
+template <typename TIn1>
+inline cudaError_t row_inv_fwd(llg_ctx *c, int logn, const RowArgs<float, TIn1, float> &a1,
+                               const RowArgs<float, float, float> &a2, int blocks, int threads, size_t sm) {
+    LLG_CT_SWITCH(logn, (row_inv_fwd_launch<TIn1, LG>(c, a1, a2, blocks, threads, sm)))
 }
 template <typename T>
 inline cudaError_t col(llg_ctx *c, int logn, int mode, const ColArgs<T> &a, dim3 grid, int TW) {
