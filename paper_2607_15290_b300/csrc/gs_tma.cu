@@ -32,12 +32,14 @@ constexpr int NC = NCW * 32;              // consumer threads (RB_THREADS: the b
 constexpr int NT = NC + 32;               // + one producer warp
 static_assert(NC == RB_THREADS, "consumer threads = reduction width");
 
-// ring shape: up to 12 basis vectors two blocks per SM with three 32 KB stages each; beyond
-// that (more registers a thread) one block per SM with four 48 KB stages
+// ring shape: up to 12 basis vectors two blocks per SM with two 48 KB stages each (measured
+// at 128^3 against three 32, three 36 and four 24 KB stages: 75.5 against 78.1, 78.8 and
+// 79.7 us a pass); beyond that (more registers a thread) one block per SM with four 48 KB
+// stages
 template <int MAXV> struct Ring {
     static constexpr int BLOCKS = MAXV <= 12 ? 2 : 1;
-    static constexpr int NS = MAXV <= 12 ? 3 : 4;
-    static constexpr int TARGET = MAXV <= 12 ? 32 * 1024 : 48 * 1024;
+    static constexpr int NS = MAXV <= 12 ? 2 : 4;
+    static constexpr int TARGET = 48 * 1024;
 };
 
 // bytes staged per vector element: w hi (+ w lo in pass C), V_0 (FP64), 8 per later vector
