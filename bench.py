@@ -55,7 +55,7 @@ ARNOLDI_TRAFFIC_BYTES = 371.3e6
 ARNOLDI_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 90 non-empty "
                         "arnoldi_pass launches of this workload (exact-count kernels, fused reduction)")
 # the same for the FP32-pair passes (gs_pass_staged), 90 launches of this workload
-PAIR_TRAFFIC_BYTES = 392.6e6
+PAIR_TRAFFIC_BYTES = 392.5e6
 PAIR_TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum averaged over 90 gs_pass_staged "
                      "launches of this workload (profiles/gs_pass_staged_128cube_dram.md)")
 

@@ -308,8 +308,9 @@ llg_status llg_set_pass_plan(llg_ctx *ctx, int plan);
    counterpart in the paper): every compiled shape (register kernel with 4/8/16-column
    tiles; shared-memory-staged FP32 kernel with several tile/sub-batch sizes) is run on a
    deterministic spectrum, its result checked against the default shape (candidates that
-   disagree beyond 1e-4 FP32 / 1e-11 FP64 relative are rejected), timed with CUDA events, and
-   the fastest kept for each pass.  precision_mask: 1 = FP64 passes, 2 = FP32 passes, 3 = both.
+   disagree beyond 1e-4 FP32 / 1e-11 FP64 relative are rejected), timed with CUDA events
+   (median of seven runs), and the fastest kept for each pass, a later candidate replacing an
+   earlier one only when at least 3% faster.  precision_mask: 1 = FP64 passes, 2 = FP32 passes, 3 = both.
    report (HOST, may be NULL): text of the timings and choices.  Allocates and frees scratch;
    synchronises the stream.  Without this call the default shapes are used. */
 llg_status llg_autotune(llg_ctx *ctx, int precision_mask, char *report, int report_len);

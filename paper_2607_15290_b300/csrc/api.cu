@@ -247,17 +247,34 @@ __global__ void __launch_bounds__(RB_THREADS) k_picard_advance(const double *__r
 // difference is formed in FP64; the squares are summed in FP32 per thread (the test compares
 // the two norms to a tolerance: six significant digits are plenty) and in FP64 across
 // threads, off the FP64 unit that the three multiply-adds a value would otherwise load.
+// (V2: two elements a thread per 16-byte access; both arrays 16-byte aligned)
+template <bool V2>
 __global__ void __launch_bounds__(RB_THREADS) k_picard_norms_advance(const double *__restrict__ v, double *__restrict__ vold,
                                                                      long long n3, double *partials) {
     long long lo, hi;
     block_chunk(n3, lo, hi);
     float s0 = 0.0f, s1 = 0.0f;
-    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-        const double ve = v[e];
-        const float d = d2f_rn(ve - vold[e]), vf = d2f_rn(ve);
+    auto one = [&](double ve, double vo) {
+        const float d = d2f_rn(ve - vo), vf = d2f_rn(ve);
         s0 = __fmaf_rn(d, d, s0);
         s1 = __fmaf_rn(vf, vf, s1);
-        vold[e] = ve;
+    };
+    if constexpr (V2) {
+        for (long long e = lo + 2 * threadIdx.x; e + 1 < hi; e += 2 * blockDim.x) {
+            const double2 ve = *reinterpret_cast<const double2 *>(v + e), vo = *reinterpret_cast<const double2 *>(vold + e);
+            one(ve.x, vo.x);
+            one(ve.y, vo.y);
+            *reinterpret_cast<double2 *>(vold + e) = ve;
+        }
+        if (((hi - lo) & 1) && threadIdx.x == 0) {
+            one(v[hi - 1], vold[hi - 1]);
+            vold[hi - 1] = v[hi - 1];
+        }
+    } else {
+        for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            one(v[e], vold[e]);
+            vold[e] = v[e];
+        }
     }
     double acc[2] = {(double)s0, (double)s1};
     block_reduce_store<2>(acc, 2, partials + (long long)blockIdx.x * RB_STRIDE);
@@ -1145,7 +1162,10 @@ llg_status llg_step_midpoint(llg_ctx *c, const llg_params *p, const llg_opts *o,
         else if (st != LLG_OK) { inf.status = st; if (info) *info = inf; return st; }
         if (it >= 1) {
             // the stopping test's norms, and vold = v in the same pass
-            k_picard_norms_advance<<<nb, RB_THREADS, 0, c->stream>>>(x_out, vold, 3 * N, c->red);
+            if ((((uintptr_t)x_out | (uintptr_t)vold) & 15u) == 0)
+                k_picard_norms_advance<true><<<nb, RB_THREADS, 0, c->stream>>>(x_out, vold, 3 * N, c->red);
+            else
+                k_picard_norms_advance<false><<<nb, RB_THREADS, 0, c->stream>>>(x_out, vold, 3 * N, c->red);
             k_sum_partials_n<<<1, RB_THREADS, 0, c->stream>>>(c->red, nb, 2, c->dsc);
             c->launches += 2;
             if ((st = sync_scalars(c, 2)) != LLG_OK) return st;

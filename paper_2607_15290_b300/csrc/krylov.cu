@@ -371,17 +371,36 @@ __global__ void __launch_bounds__(RB_THREADS) cycle_update_pair4(double *x, cons
     }
 }
 
-// out = b - t, partial sums of out^2
+// out = b - t, partial sums of out^2 (two elements a thread per 16-byte access when all three
+// arrays are 16-byte aligned: the blocks' chunks start at even elements)
+template <bool V2>
 __global__ void __launch_bounds__(RB_THREADS) residual_partials(const double *__restrict__ b, const double *t,
                                                                 double *out, long long n, double *partials) {
     pdl_wait();
     double acc[1] = {0.0};
     long long lo, hi;
     block_chunk(n, lo, hi);
-    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-        const double r = b[e] - t[e];
-        out[e] = r;
-        acc[0] += r * r;
+    if constexpr (V2) {
+        double a1 = 0.0;
+        for (long long e = lo + 2 * threadIdx.x; e + 1 < hi; e += 2 * blockDim.x) {
+            const double2 bb = *reinterpret_cast<const double2 *>(b + e), tt = *reinterpret_cast<const double2 *>(t + e);
+            const double2 r = make_double2(bb.x - tt.x, bb.y - tt.y);
+            *reinterpret_cast<double2 *>(out + e) = r;
+            acc[0] += r.x * r.x;
+            a1 += r.y * r.y;
+        }
+        if (((hi - lo) & 1) && threadIdx.x == 0) {   // an odd chunk (the last one)
+            const double r = b[hi - 1] - t[hi - 1];
+            out[hi - 1] = r;
+            a1 += r * r;
+        }
+        acc[0] += a1;
+    } else {
+        for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            const double r = b[e] - t[e];
+            out[e] = r;
+            acc[0] += r * r;
+        }
     }
     block_reduce_store<1>(acc, 1, partials + (long long)blockIdx.x * 64);
 }
@@ -416,7 +435,9 @@ llg_status dot_async(llg_ctx *c, const double *a, const double *b, long long n, 
 
 static llg_status residual_async(llg_ctx *c, const double *b, const double *t, double *out, long long n, double *dst_dev) {
     const int nb = reduction_blocks(c);
-    launch_pdl(residual_partials, dim3(nb), dim3(RB_THREADS), 0, c->stream, b, t, out, n, c->red);
+    const bool v2 = (((uintptr_t)b | (uintptr_t)t | (uintptr_t)out) & 15u) == 0;
+    if (v2) launch_pdl(residual_partials<true>, dim3(nb), dim3(RB_THREADS), 0, c->stream, b, t, out, n, c->red);
+    else launch_pdl(residual_partials<false>, dim3(nb), dim3(RB_THREADS), 0, c->stream, b, t, out, n, c->red);
     launch_pdl(sum_partials, dim3(1), dim3(RB_THREADS), 0, c->stream, c->red, nb, dst_dev);
     c->launches += 2;
     return cuda_check(c, cudaGetLastError(), "residual");

@@ -561,16 +561,22 @@ static llg_status tune_prec(llg_ctx *c, std::string *report) {
             for (int b = 0; b < 512; ++b) { d = std::max(d, hp[2 * b]); m = std::max(m, hp[2 * b + 1]); }
             const double tol = sizeof(T) == 4 ? 1e-4 : 1e-11;
             if (!(d <= tol * m)) { rep += " " + cfg_name(f) + "=rejected"; continue; }
-            float tot = 0.f, ms = 0.f;
-            for (int r = 0; r < 5; ++r) {
+            // median of seven timed runs; a later candidate replaces the best so far only when
+            // it is at least 3% faster, so that near-ties keep the earlier (register, paired,
+            // TMA-fed) shapes instead of following timing noise
+            constexpr int REPS = 7;
+            float t[REPS], ms = 0.f;
+            int got = 0;
+            for (; got < REPS; ++got) {
                 if ((e = run_once(f, &ms)) != cudaSuccess) break;
-                tot += ms;
+                t[got] = ms;
             }
             if (e != cudaSuccess) { cudaGetLastError(); continue; }
-            tot /= 5.f;
+            std::sort(t, t + REPS);
+            const float tot = t[REPS / 2];
             snprintf(line, sizeof line, " %s=%.1fus", cfg_name(f).c_str(), tot * 1e3f);
             rep += line;
-            if (tot < best_ms) { best_ms = tot; best = f; }
+            if (tot < 0.97f * best_ms) { best_ms = tot; best = f; }
         }
         c->colcfg[pi][slot] = best;
         *report += rep + " -> " + cfg_name(best) + "\n";
