@@ -359,8 +359,12 @@ __device__ __forceinline__ void row_inv_ct_body(const RowArgs<T, TIn, TOut> &a, 
 
 // FP32-pair blocks (at most 3 x 128 threads) are held to 85 registers so that three blocks of
 // a 128-point row group fit an SM: the pair epilogue is latency-bound at two
+template <typename T> struct RowInvBounds {
+    static constexpr int threads = is_fpair<T>::value ? 384 : (sizeof(T) == 4 ? 256 : 512);
+    static constexpr int blocks = is_fpair<T>::value ? 2 : (sizeof(T) == 4 ? 3 : 1);
+};
 template <typename T, typename TIn, typename TOut, int LOGN, int OUT>
-__global__ void __launch_bounds__(is_fpair<T>::value ? 384 : 512, is_fpair<T>::value ? 2 : 1) row_inv_ct(RowArgs<T, TIn, TOut> a) {
+__global__ void __launch_bounds__(RowInvBounds<T>::threads, RowInvBounds<T>::blocks) row_inv_ct(RowArgs<T, TIn, TOut> a) {
     pdl_wait();
     if (a.io.skip && *a.io.skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
