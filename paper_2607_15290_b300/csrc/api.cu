@@ -226,20 +226,34 @@ __global__ void __launch_bounds__(RB_THREADS) k_picard_advance(const double *__r
                                                                double *partials) {
     const double *rprev = r;
     double *r0 = r;
-    double acc[1] = {0.0};
+    f32x2 sq{0.0f, 0.0f};
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
         const double v1 = x[j], v2 = x[N + j], v3 = x[2 * N + j], r = x[3 * N + j];
         const double a1 = m[j] + hk * v1, a2 = m[N + j] + hk * v2, a3 = m[2 * N + j] + hk * v3;
         const double d1 = a1 - mhat[j], d2 = a2 - mhat[N + j], d3 = a3 - mhat[2 * N + j];
-        r0[j] = rprev[j] - (d2 * v3 - d3 * v2 + d1 * r);
-        r0[N + j] = rprev[N + j] - (d3 * v1 - d1 * v3 + d2 * r);
-        r0[2 * N + j] = rprev[2 * N + j] - (d1 * v2 - d2 * v1 + d3 * r);
-        r0[3 * N + j] = rprev[3 * N + j] + (d1 * v1 + d2 * v2 + d3 * v3);
+        // the change of the nodal blocks and the squared norm in FP32-pair arithmetic (off the
+        // FP64 unit): dm is small beside m, and its terms carry about 47 bits, far below the FP64
+        // rounding of r0 itself; mhat and r0 stay FP64
+        const fpair D1 = cvt<fpair>(d1), D2 = cvt<fpair>(d2), D3 = cvt<fpair>(d3);
+        const fpair V1 = cvt<fpair>(v1), V2 = cvt<fpair>(v2), V3 = cvt<fpair>(v3), R = cvt<fpair>(r);
+        const double q0 = rprev[j] - cvt<double>(fp_dot2(D2, V3, -D3, V2) + D1 * R);
+        const double q1 = rprev[N + j] - cvt<double>(fp_dot2(D3, V1, -D1, V3) + D2 * R);
+        const double q2 = rprev[2 * N + j] - cvt<double>(fp_dot2(D1, V2, -D2, V1) + D3 * R);
+        const double q3 = rprev[3 * N + j] + cvt<double>(fp_dot2(D1, V1, D2, V2) + D3 * V3);
+        r0[j] = q0;
+        r0[N + j] = q1;
+        r0[2 * N + j] = q2;
+        r0[3 * N + j] = q3;
         mhat[j] = a1;
         mhat[N + j] = a2;
         mhat[2 * N + j] = a3;
-        acc[0] += r0[j] * r0[j] + r0[N + j] * r0[N + j] + r0[2 * N + j] * r0[2 * N + j] + r0[3 * N + j] * r0[3 * N + j];
+        const f32x2 p0 = split_f64(q0), p1 = split_f64(q1), p2 = split_f64(q2), p3 = split_f64(q3);
+        fma_acc(p0, p0, sq);
+        fma_acc(p1, p1, sq);
+        fma_acc(p2, p2, sq);
+        fma_acc(p3, p3, sq);
     }
+    double acc[1] = {pair_to_f64(sq)};
     block_reduce_store<1>(acc, 1, partials + (long long)blockIdx.x * RB_STRIDE);
 }
 
