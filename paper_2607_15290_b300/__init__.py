@@ -26,6 +26,20 @@ __all__ = [
 ]
 
 
+def parse_axis_shape(shape):
+    """(kind, E, TW, CB) of an axis-pass shape in the autotuner's notation: register(E8,TW16),
+    staged(TW32,CB16), paired(E8,TW16), tma(TW8), tma(E16,TW8)."""
+    import re
+    m = re.fullmatch(r"(register|staged|paired|tma)\((.*)\)", shape.strip())
+    if not m:
+        raise ValueError(f"unknown axis shape {shape!r}")
+    kv = dict(re.findall(r"([A-Z]+)(\d+)", m.group(2)))
+    if not kv.get("TW") or set(kv) - {"E", "TW", "CB"}:
+        raise ValueError(f"unknown axis shape {shape!r}")
+    kind = {"register": 0, "staged": 1, "paired": 3, "tma": 4}[m.group(1)]
+    return kind, int(kv.get("E", 8)), int(kv["TW"]), int(kv.get("CB", 0))
+
+
 class LLGError(RuntimeError):
     def __init__(self, status, msg, info=None):
         super().__init__(f"{_abi.STATUS.get(status, status)}: {msg}")
@@ -141,14 +155,9 @@ class Context:
     def set_axis_shape(self, slot, shape, fp32=True):
         """Set one axis pass's launch shape by the tuner's name for it, e.g.
         set_axis_shape("z", "tma(TW8)") or set_axis_shape("y-forward", "register(E8,TW16)")."""
-        import re
-        m = re.fullmatch(r"(register|staged|paired|tma)\((.*)\)", shape.strip())
-        if not m:
-            raise ValueError(f"unknown axis shape {shape!r}")
-        kv = dict(re.findall(r"([A-Z]+)(\d+)", m.group(2)))
-        kind = {"register": 0, "staged": 1, "paired": 3, "tma": 4}[m.group(1)]
-        E = int(kv.get("E", 8))
-        TW, CB = int(kv.get("TW", 0)), int(kv.get("CB", 0))
+        kind, E, TW, CB = parse_axis_shape(shape)
+        if slot not in self._SLOTS:
+            raise ValueError(f"unknown axis-pass slot {slot!r}")
         self._check(self.lib.llg_set_axis_shape(self.h, int(fp32), self._SLOTS[slot], kind, E, TW, CB))
 
     def profile_begin(self, kernel_class):

@@ -48,3 +48,16 @@ def test_host_side_argument_errors():
     assert L.llg_create(None, None, C.byref(h)) == 1
     assert L.llg_saddle_apply(None, None, None, None, None, 0) == 1
     assert L.llg_last_error(None) == b"null context"
+
+
+def test_axis_shape_names():
+    """The autotuner's shape names parse to the (kind, E, TW, CB) the C ABI takes."""
+    from paper_2607_15290_b300 import parse_axis_shape
+    assert parse_axis_shape("register(E8,TW16)") == (0, 8, 16, 0)
+    assert parse_axis_shape("staged(TW32,CB16)") == (1, 8, 32, 16)
+    assert parse_axis_shape("paired(E8,TW16)") == (3, 8, 16, 0)
+    assert parse_axis_shape("tma(TW8)") == (4, 8, 8, 0)
+    assert parse_axis_shape(" tma(E16,TW16) ") == (4, 16, 16, 0)
+    for bad in ("tma", "tma()", "cufft(TW8)", "register(E8)", "register(E8,TW16,X3)"):
+        with pytest.raises(ValueError):
+            parse_axis_shape(bad)
