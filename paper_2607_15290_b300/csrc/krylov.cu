@@ -381,20 +381,24 @@ __global__ void __launch_bounds__(RB_THREADS) residual_partials(const double *__
     long long lo, hi;
     block_chunk(n, lo, hi);
     if constexpr (V2) {
-        double a1 = 0.0;
+        // the squares summed in FP32-pair arithmetic (off the FP64 unit, which the subtraction
+        // alone then loads): about 47 bits, far more than the convergence test needs
+        f32x2 s0{0.0f, 0.0f}, s1{0.0f, 0.0f};
         for (long long e = lo + 2 * threadIdx.x; e + 1 < hi; e += 2 * blockDim.x) {
             const double2 bb = *reinterpret_cast<const double2 *>(b + e), tt = *reinterpret_cast<const double2 *>(t + e);
             const double2 r = make_double2(bb.x - tt.x, bb.y - tt.y);
             *reinterpret_cast<double2 *>(out + e) = r;
-            acc[0] += r.x * r.x;
-            a1 += r.y * r.y;
+            const f32x2 px = split_f64(r.x), py = split_f64(r.y);
+            fma_acc(px, px, s0);
+            fma_acc(py, py, s1);
         }
         if (((hi - lo) & 1) && threadIdx.x == 0) {   // an odd chunk (the last one)
             const double r = b[hi - 1] - t[hi - 1];
             out[hi - 1] = r;
-            a1 += r * r;
+            const f32x2 pr = split_f64(r);
+            fma_acc(pr, pr, s1);
         }
-        acc[0] += a1;
+        acc[0] = pair_to_f64(s0) + pair_to_f64(s1);
     } else {
         for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
             const double r = b[e] - t[e];
